@@ -1,0 +1,206 @@
+/*
+ * megopolis.h -- C ABI of libmegopolis.so, GB300 (sm_103a) resampling.
+ *
+ * Metropolis-style resampling of a float32 weight vector into int32
+ * ancestor indices, after "The Megopolis Resampler: Memory Coalesced
+ * Resampling on GPUs" (arXiv 2109.13504):
+ *   - Megopolis (Algorithm 5, Section 4): iteration b proposes, for particle
+ *     i, j = (i_aligned + o_aligned + (i + o^(b)) mod 32) mod N with one
+ *     offset o^(b) shared by every particle;
+ *   - Metropolis (Algorithm 2, Section 3): an independent uniform j per
+ *     particle and iteration (the baseline);
+ *   - Metropolis-C1 / -C2 (Algorithms 3, 4, Section 3.1): j uniform inside a
+ *     partition of P_size bytes chosen per warp once (C1) or per iteration
+ *     (C2).
+ * Every variant accepts j when fl(u * w_k) <= w_j (u in (0,1], binary32,
+ * round to nearest), the division-free form of u <= w_j / w_k.
+ *
+ * Random numbers: Philox4x32-10 keyed by `seed`, counters carry the
+ * particle, the iteration, `stream_id` and a per-purpose tag.  Ancestors are
+ * a pure function of (weight bits, n, B, seed, stream_id, variant, P_size):
+ * they do not depend on the launch shape, the memory path or the stream.
+ *
+ * Conventions for every entry point:
+ *   - Pointers prefixed d_ are device pointers, h_ host pointers.  The caller
+ *     owns every buffer; nothing here allocates device memory, and nothing
+ *     keeps a pointer after the call returns (work is queued on `stream`).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *   - Argument errors are detected on the host and returned synchronously;
+ *     nothing is launched then.  Errors found on the device (bad weights,
+ *     a bound beyond its cap) are written to a caller-provided int32 status
+ *     word, read with mego_sync_status.  Nothing calls abort() or exit().
+ *   - Weights need not be normalised (Section 7; Section 8).
+ *   - n >= 1 and n <= MEGO_N_MAX; 0 <= B <= MEGO_B_MAX.
+ */
+#ifndef MEGOPOLIS_H
+#define MEGOPOLIS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MEGO_ABI_VERSION 1
+#define MEGO_N_MAX (1 << 30)
+#define MEGO_B_MAX (1 << 24)
+
+typedef enum mego_status {
+  MEGO_OK = 0,
+  MEGO_EINVAL = 1,    /* bad argument; nothing was launched              */
+  MEGO_ENOMEM = 2,    /* caller workspace too small                       */
+  MEGO_ECUDA = 3,     /* a CUDA runtime call failed                       */
+  MEGO_ETIMEOUT = 4,  /* mego_sync_status: deadline passed                */
+  MEGO_EWEIGHTS = 5   /* device: NaN/Inf/negative or all-zero weights, or
+                         B above the cap                                  */
+} mego_status;
+
+typedef enum mego_variant {
+  MEGO_MEGOPOLIS = 0,
+  MEGO_METROPOLIS = 1,
+  MEGO_METROPOLIS_C1 = 2,
+  MEGO_METROPOLIS_C2 = 3
+} mego_variant;
+
+typedef enum mego_layout {
+  MEGO_LAYOUT_SOA = 0,  /* x[d * ld + i], d < dim                         */
+  MEGO_LAYOUT_AOS4 = 1  /* four floats per particle, x[4 * i + c]; 16-byte
+                           aligned; one 128-bit load and store per particle */
+} mego_layout;
+
+typedef enum mego_path {
+  MEGO_PATH_AUTO = 0,
+  MEGO_PATH_GLOBAL = 1, /* weights read from L2/HBM with coalesced loads  */
+  MEGO_PATH_SMEM = 2    /* weights staged whole in shared memory by a bulk
+                           async copy; needs 4n bytes <= the CTA's limit  */
+} mego_path;
+
+/* Launch shape.  Any field 0 selects the library's choice.  The result
+ * never depends on these. */
+typedef struct mego_launch_cfg {
+  int32_t threads;      /* CTA size, a multiple of 32 in [64, 256]         */
+  int32_t ppt;          /* particles per thread, 1, 2 or 4 (each a 32-particle
+                           segment of one warp)                              */
+  int32_t path;         /* mego_path                                         */
+  int32_t ctas_per_sm;  /* resident CTAs per SM to aim for                   */
+} mego_launch_cfg;
+
+/* ABI version (MEGO_ABI_VERSION) and a static text for a status code. */
+int mego_abi_version(void);
+const char* mego_status_string(int status);
+
+/* ----------------------------------------------------------------------
+ * Resample (Algorithm 5 / Algorithm 2 / Algorithms 3-4), B given by the host.
+ *   d_w      [n] float32, finite and >= 0 (not checked here; use
+ *            mego_compute_B to validate).  Read-only.
+ *   B        number of iterations, 0 <= B <= MEGO_B_MAX; B = 0 gives
+ *            ancestors equal to the particle index.
+ *   d_anc    [n] int32 output, must not overlap d_w.
+ * Returns MEGO_EINVAL for a null pointer, n out of range, B out of range,
+ * an unknown variant or overlapping buffers; MEGO_ECUDA if the launch fails.
+ */
+mego_status mego_resample(const float* d_w, int32_t n, int32_t B, uint64_t seed,
+                          uint32_t stream_id, int variant, int32_t* d_anc,
+                          void* stream);
+
+/* ----------------------------------------------------------------------
+ * Resample and gather particle state by ancestor: x_out^(i) = x_in^(k)
+ * (last line of Algorithms 2 and 5).
+ *   B / d_B      if d_B is non-NULL the iteration count is read on the
+ *                device from *d_B (as written by mego_compute_B); a value
+ *                < 0 there means "bound failed" and the kernel writes
+ *                nothing.  Otherwise the host value B is used.
+ *   psize_bytes  P_size for C1/C2 (a multiple of 4 with P_size/4 dividing
+ *                n); ignored by the other variants.
+ *   d_x_in/out   state, layout mego_layout; SoA: dim rows of stride ld >= n
+ *                floats; AoS4: dim must be 4, ld ignored, both 16-byte
+ *                aligned.  May both be NULL (no gather).  Must not overlap.
+ *   d_anc        [n] int32 output; may be NULL when gathering.
+ *   cfg          launch shape, or NULL.
+ */
+mego_status mego_resample_gather(const float* d_w, int32_t n, int32_t B,
+                                 const int32_t* d_B, uint64_t seed,
+                                 uint32_t stream_id, int variant,
+                                 uint32_t psize_bytes, const float* d_x_in,
+                                 float* d_x_out, int32_t dim, int64_t ld,
+                                 int layout, int32_t* d_anc,
+                                 const mego_launch_cfg* cfg, void* stream);
+
+/* ----------------------------------------------------------------------
+ * Iteration bound, Eq. 3 (Section 3) and Proposition 1 (Eq. 4):
+ *   B = ceil(log(eps) / log(1 - E(w)/max(w)))
+ * with E(w) the sample mean (summed in double, fixed order) and max(w) the
+ * sample maximum.  eps in (0, 1].  E(w) = max(w) or eps = 1 gives B = 0.
+ *   d_B       [1] int32 output: B, or -1 on a device-side error.
+ *   d_status  [1] int32 output: MEGO_OK, or MEGO_EWEIGHTS when a weight is
+ *             NaN, infinite or negative, all weights are 0, or B > b_max.
+ *   d_q       [1] double output, the value before the ceiling; may be NULL.
+ *   b_max     cap on B, 0 < b_max <= MEGO_B_MAX.
+ *   d_ws      caller workspace of at least mego_workspace_bytes(n) bytes,
+ *             256-byte aligned; its contents need no initialisation.
+ * Two kernels, no host synchronisation: graph-capturable.
+ */
+size_t mego_workspace_bytes(int32_t n);
+mego_status mego_compute_B(const float* d_w, int32_t n, double eps,
+                           int32_t b_max, int32_t* d_B, int32_t* d_status,
+                           double* d_q, void* d_ws, size_t ws_bytes,
+                           void* stream);
+
+/* ----------------------------------------------------------------------
+ * Likelihood weights fused with the bound: w_i = exp(-(x_i - y)^2 / 2)
+ * from row 0 of an SoA state (Eq. 12 without its constant factor, the
+ * update of Algorithm 1), then B as in mego_compute_B.
+ *   d_x   state row 0, [n] float32 (row 0 of an SoA array).
+ *   d_w   [n] float32 output weights.
+ * Other arguments as in mego_compute_B.  expf is CUDA's single-precision
+ * exponential; it can differ from a double-precision evaluation by a few
+ * units in the last place.
+ */
+mego_status mego_likelihood_B(const float* d_x, int32_t n, float y, double eps,
+                              int32_t b_max, float* d_w, int32_t* d_B,
+                              int32_t* d_status, double* d_q, void* d_ws,
+                              size_t ws_bytes, void* stream);
+
+/* ----------------------------------------------------------------------
+ * End-to-end call on host buffers (for callers without device memory
+ * management of their own): copies h_w to d_w, computes B (if B < 0, from
+ * eps) and the ancestors, copies them to h_anc and B to *h_B, and waits for
+ * the stream.  d_w [n] float32, d_anc [n] int32, d_ws (see above) and a
+ * 16-byte device scalar area d_scalars (>= 32 bytes) are caller-provided
+ * device buffers.  Host buffers should be page-locked for full copy speed.
+ * Returns MEGO_EWEIGHTS if the bound failed on the device.
+ */
+mego_status mego_resample_host(const float* h_w, int32_t n, int32_t B,
+                               double eps, uint64_t seed, uint32_t stream_id,
+                               int variant, int32_t* h_anc, int32_t* h_B,
+                               float* d_w, int32_t* d_anc, void* d_scalars,
+                               void* d_ws, size_t ws_bytes, void* stream);
+
+/* ----------------------------------------------------------------------
+ * Wait for `stream` up to timeout_s seconds by polling an event, then copy
+ * the device status word to *h_status.  Returns MEGO_ETIMEOUT (and leaves
+ * *h_status untouched) if the stream has not drained by the deadline. */
+mego_status mego_sync_status(const int32_t* d_status, void* stream,
+                             double timeout_s, int32_t* h_status);
+
+/* ----------------------------------------------------------------------
+ * Measurement helper (not part of the method): read `bytes` of d_buf
+ * `reps` times with coalesced 128-bit loads, writing one float per CTA to
+ * d_sink (at least four floats per SM) so the reads are not elided.  Used to
+ * measure the L2 bandwidth that bounds the global-memory path when d_buf is
+ * smaller than L2.  bytes must be a multiple of 16 and d_buf 16-byte
+ * aligned.
+ */
+mego_status mego_probe_read(const void* d_buf, size_t bytes, int32_t reps,
+                            float* d_sink, void* stream);
+
+/* Kernel launches the library queued since the process started (host-side
+ * count; lets a caller confirm that the CUDA path ran). */
+uint64_t mego_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MEGOPOLIS_H */

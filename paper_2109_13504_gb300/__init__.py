@@ -1,0 +1,313 @@
+"""Python binding for libmegopolis.so (Megopolis / Metropolis resampling on
+GB300).  Argument marshalling only: every step runs in the library's CUDA
+kernels.  torch supplies device memory and the current CUDA stream.
+
+The functions carry the C ABI's names (``mego_resample``,
+``mego_resample_gather``, ``mego_compute_B``, ``mego_likelihood_B``,
+``mego_resample_host``, ``mego_sync_status``, ``mego_probe_read``); they take
+torch tensors instead of raw pointers and raise ``MegoError`` on a non-OK
+status.  ``resample`` is a convenience wrapper that allocates the output.
+
+If the shared library has not been built (``__graft_entry__.build()`` or
+``python -m paper_2109_13504_gb300.build``) every call raises: there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libmegopolis.so")
+
+MEGO_OK = 0
+MEGO_EINVAL = 1
+MEGO_ENOMEM = 2
+MEGO_ECUDA = 3
+MEGO_ETIMEOUT = 4
+MEGO_EWEIGHTS = 5
+
+MEGOPOLIS = 0
+METROPOLIS = 1
+METROPOLIS_C1 = 2
+METROPOLIS_C2 = 3
+
+LAYOUT_SOA = 0
+LAYOUT_AOS4 = 1
+
+PATH_AUTO = 0
+PATH_GLOBAL = 1
+PATH_SMEM = 2
+
+N_MAX = 1 << 30
+B_MAX = 1 << 24
+
+
+class MegoError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__("%s: %s (status %d)" % (what, status_string(status), status))
+
+
+class LaunchCfg(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32), ("ppt", ctypes.c_int32),
+                ("path", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(
+            "libmegopolis.so is not built (%s); run __graft_entry__.build() -- "
+            "there is no CPU fallback" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, u32, u64, f64, sz = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32,
+                                  ctypes.c_uint64, ctypes.c_double, ctypes.c_size_t)
+    ci = ctypes.c_int
+    sigs = {
+        "mego_abi_version": ([], ci),
+        "mego_status_string": ([ci], ctypes.c_char_p),
+        "mego_launch_count": ([], u64),
+        "mego_workspace_bytes": ([i32], sz),
+        "mego_resample": ([vp, i32, i32, u64, u32, ci, vp, vp], ci),
+        "mego_resample_gather": ([vp, i32, i32, vp, u64, u32, ci, u32, vp, vp, i32,
+                                  ctypes.c_int64, ci, vp, ctypes.POINTER(LaunchCfg), vp],
+                                 ci),
+        "mego_compute_B": ([vp, i32, f64, i32, vp, vp, vp, vp, sz, vp], ci),
+        "mego_likelihood_B": ([vp, i32, ctypes.c_float, f64, i32, vp, vp, vp, vp, vp,
+                               sz, vp], ci),
+        "mego_resample_host": ([vp, i32, i32, f64, u64, u32, ci, vp, vp, vp, vp, vp, vp,
+                                sz, vp], ci),
+        "mego_sync_status": ([vp, vp, f64, vp], ci),
+        "mego_probe_read": ([vp, sz, i32, vp, vp], ci),
+    }
+    for name, (args, res) in sigs.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def loaded_library_path() -> str:
+    _load()
+    return LIB_PATH
+
+
+def status_string(status: int) -> str:
+    try:
+        return _load().mego_status_string(int(status)).decode()
+    except Exception:
+        return "status"
+
+
+def abi_version() -> int:
+    return int(_load().mego_abi_version())
+
+
+def launch_count() -> int:
+    return int(_load().mego_launch_count())
+
+
+def workspace_bytes(n: int) -> int:
+    return int(_load().mego_workspace_bytes(int(n)))
+
+
+def _check(status: int, what: str) -> None:
+    if status != MEGO_OK:
+        raise MegoError(status, what)
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _dev(t: torch.Tensor, dtype, name: str, numel: Optional[int] = None) -> int:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must have dtype %s" % (name, dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if numel is not None and t.numel() < numel:
+        raise ValueError("%s has %d elements, needs %d" % (name, t.numel(), numel))
+    return t.data_ptr()
+
+
+def _cfg(cfg) -> Optional[LaunchCfg]:
+    if cfg is None:
+        return None
+    if isinstance(cfg, dict):
+        cfg = LaunchCfg(**{k: int(v) for k, v in cfg.items()})
+    return cfg
+
+
+# --------------------------------------------------------------------------
+# C-ABI wrappers
+
+
+def mego_resample(w: torch.Tensor, B: int, seed: int, stream_id: int = 0,
+                  variant: int = MEGOPOLIS, anc: Optional[torch.Tensor] = None,
+                  stream=None) -> torch.Tensor:
+    n = w.numel()
+    if anc is None:
+        anc = torch.empty(n, dtype=torch.int32, device=w.device)
+    st = _load().mego_resample(_dev(w, torch.float32, "w"), n, int(B), int(seed),
+                               int(stream_id), int(variant),
+                               _dev(anc, torch.int32, "anc", n), _stream(stream))
+    _check(st, "mego_resample")
+    return anc
+
+
+def mego_resample_gather(w: torch.Tensor, B: int = 0, B_dev: Optional[torch.Tensor] = None,
+                         seed: int = 0, stream_id: int = 0, variant: int = MEGOPOLIS,
+                         psize_bytes: int = 0, x_in: Optional[torch.Tensor] = None,
+                         x_out: Optional[torch.Tensor] = None, layout: int = LAYOUT_SOA,
+                         anc: Optional[torch.Tensor] = None, cfg=None, stream=None):
+    """Resample and (optionally) gather state.  SoA state is [dim, n] (row
+    stride = its second dimension); AoS4 state is [n, 4]."""
+    n = w.numel()
+    dim, ld = 0, 0
+    px_in = px_out = None
+    if x_in is not None or x_out is not None:
+        if x_in is None or x_out is None:
+            raise ValueError("x_in and x_out go together")
+        if layout == LAYOUT_SOA:
+            if x_in.dim() != 2 or x_in.shape[1] < n or x_out.shape != x_in.shape:
+                raise ValueError("SoA state must be [dim, >= n] and x_out the same shape")
+            dim, ld = x_in.shape[0], x_in.shape[1]
+        else:
+            if x_in.shape != (n, 4) or x_out.shape != (n, 4):
+                raise ValueError("AoS4 state must be [n, 4]")
+            dim, ld = 4, 4
+        px_in = _dev(x_in, torch.float32, "x_in")
+        px_out = _dev(x_out, torch.float32, "x_out")
+    panc = _dev(anc, torch.int32, "anc", n) if anc is not None else None
+    pB = _dev(B_dev, torch.int32, "B_dev", 1) if B_dev is not None else None
+    c = _cfg(cfg)
+    st = _load().mego_resample_gather(
+        _dev(w, torch.float32, "w"), n, int(B), pB, int(seed), int(stream_id), int(variant),
+        int(psize_bytes), px_in, px_out, int(dim), int(ld), int(layout), panc,
+        ctypes.byref(c) if c is not None else None, _stream(stream))
+    _check(st, "mego_resample_gather")
+    return anc, x_out
+
+
+def _scalars(device, B_dev, status, q):
+    if B_dev is None:
+        B_dev = torch.empty(1, dtype=torch.int32, device=device)
+    if status is None:
+        status = torch.empty(1, dtype=torch.int32, device=device)
+    if q is None:
+        q = torch.empty(1, dtype=torch.float64, device=device)
+    return B_dev, status, q
+
+
+def _workspace(n, device, ws):
+    need = workspace_bytes(n)
+    if ws is None:
+        ws = torch.empty(need, dtype=torch.uint8, device=device)
+    return ws, need
+
+
+def mego_compute_B(w: torch.Tensor, eps: float = 0.01, b_max: int = B_MAX,
+                   B_dev=None, status=None, q=None, ws=None, stream=None):
+    """Eq. 3 on the device.  Returns (B_dev, status, q) device tensors."""
+    n = w.numel()
+    B_dev, status, q = _scalars(w.device, B_dev, status, q)
+    ws, _ = _workspace(n, w.device, ws)
+    st = _load().mego_compute_B(_dev(w, torch.float32, "w"), n, float(eps), int(b_max),
+                                _dev(B_dev, torch.int32, "B_dev", 1),
+                                _dev(status, torch.int32, "status", 1),
+                                _dev(q, torch.float64, "q", 1),
+                                _dev(ws, torch.uint8, "ws"), ws.numel(), _stream(stream))
+    _check(st, "mego_compute_B")
+    return B_dev, status, q
+
+
+def mego_likelihood_B(x0: torch.Tensor, y: float, eps: float = 0.01, b_max: int = B_MAX,
+                      w: Optional[torch.Tensor] = None, B_dev=None, status=None, q=None,
+                      ws=None, stream=None):
+    """w = exp(-(x0 - y)^2/2) and Eq. 3.  Returns (w, B_dev, status, q)."""
+    n = x0.numel()
+    if w is None:
+        w = torch.empty(n, dtype=torch.float32, device=x0.device)
+    B_dev, status, q = _scalars(x0.device, B_dev, status, q)
+    ws, _ = _workspace(n, x0.device, ws)
+    st = _load().mego_likelihood_B(_dev(x0, torch.float32, "x0"), n, ctypes.c_float(y),
+                                   float(eps), int(b_max), _dev(w, torch.float32, "w", n),
+                                   _dev(B_dev, torch.int32, "B_dev", 1),
+                                   _dev(status, torch.int32, "status", 1),
+                                   _dev(q, torch.float64, "q", 1),
+                                   _dev(ws, torch.uint8, "ws"), ws.numel(), _stream(stream))
+    _check(st, "mego_likelihood_B")
+    return w, B_dev, status, q
+
+
+def mego_resample_host(h_w: torch.Tensor, B: int, eps: float, seed: int, stream_id: int,
+                       variant: int, h_anc: torch.Tensor, d_w: torch.Tensor,
+                       d_anc: torch.Tensor, d_scalars: torch.Tensor, ws: torch.Tensor,
+                       stream=None) -> int:
+    """End-to-end call on host tensors (pinned for full speed).  Returns B."""
+    n = h_w.numel()
+    if h_w.is_cuda or h_anc.is_cuda:
+        raise TypeError("h_w and h_anc must be host tensors")
+    if h_w.dtype != torch.float32 or h_anc.dtype != torch.int32:
+        raise TypeError("h_w float32, h_anc int32")
+    if not (h_w.is_contiguous() and h_anc.is_contiguous()) or h_anc.numel() < n:
+        raise ValueError("host tensors must be contiguous and large enough")
+    hB = ctypes.c_int32(-1)
+    st = _load().mego_resample_host(
+        h_w.data_ptr(), n, int(B), float(eps), int(seed), int(stream_id), int(variant),
+        h_anc.data_ptr(), ctypes.addressof(hB), _dev(d_w, torch.float32, "d_w", n),
+        _dev(d_anc, torch.int32, "d_anc", n), _dev(d_scalars, torch.uint8, "d_scalars", 32),
+        _dev(ws, torch.uint8, "ws"), ws.numel(), _stream(stream))
+    _check(st, "mego_resample_host")
+    return int(hB.value)
+
+
+def mego_sync_status(status: torch.Tensor, timeout_s: float = 10.0, stream=None) -> int:
+    h = ctypes.c_int32(-1)
+    st = _load().mego_sync_status(_dev(status, torch.int32, "status", 1), _stream(stream),
+                                  float(timeout_s), ctypes.addressof(h))
+    _check(st, "mego_sync_status")
+    return int(h.value)
+
+
+def mego_probe_read(buf: torch.Tensor, reps: int, sink: torch.Tensor, stream=None) -> None:
+    if not buf.is_cuda or not buf.is_contiguous():
+        raise TypeError("buf must be a contiguous CUDA tensor")
+    st = _load().mego_probe_read(buf.data_ptr(), buf.numel() * buf.element_size(), int(reps),
+                                 _dev(sink, torch.float32, "sink"), _stream(stream))
+    _check(st, "mego_probe_read")
+
+
+# --------------------------------------------------------------------------
+# Convenience
+
+
+def resample(w: torch.Tensor, B: Optional[int] = None, eps: float = 0.01, seed: int = 0,
+             stream_id: int = 0, variant: int = MEGOPOLIS, psize_bytes: int = 0,
+             cfg=None, stream=None) -> torch.Tensor:
+    """Ancestors as an int32 CUDA tensor.  B=None computes B from eps on the
+    device (Eq. 3) without a host synchronisation."""
+    n = w.numel()
+    anc = torch.empty(n, dtype=torch.int32, device=w.device)
+    if B is None:
+        B_dev, _, _ = mego_compute_B(w, eps, stream=stream)
+        mego_resample_gather(w, 0, B_dev, seed, stream_id, variant, psize_bytes, anc=anc,
+                             cfg=cfg, stream=stream)
+    else:
+        mego_resample_gather(w, int(B), None, seed, stream_id, variant, psize_bytes, anc=anc,
+                             cfg=cfg, stream=stream)
+    return anc

@@ -1,0 +1,190 @@
+// bound.cu -- weight reduction and the iteration bound (Eq. 3), optionally
+// fused with the likelihood weight (Eq. 12), plus a read-bandwidth probe.
+//
+// Deterministic: a fixed grid writes one partial (max, double sum, bad flag)
+// per CTA; a single CTA then folds the partials in index order.  The result
+// depends only on n and the weight bits.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "bound.cuh"
+#include "device_common.cuh"
+
+namespace mego {
+
+namespace {
+
+struct Acc {
+  float mx;
+  int bad;
+  double sum;
+};
+
+__device__ __forceinline__ void acc_add(Acc& a, float v) {
+  a.bad |= (!(v >= 0.0f) || isinf(v)) ? 1 : 0;
+  a.mx = fmaxf(a.mx, v);
+  a.sum += static_cast<double>(v);
+}
+
+__device__ __forceinline__ void acc_merge(Acc& a, const Acc& b) {
+  a.bad |= b.bad;
+  a.mx = fmaxf(a.mx, b.mx);
+  a.sum += b.sum;
+}
+
+// Warp then CTA reduction in a fixed tree order; result valid in thread 0.
+__device__ __forceinline__ Acc block_reduce(Acc a) {
+  __shared__ Acc s[32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    Acc o;
+    o.mx = __shfl_down_sync(0xFFFFFFFFu, a.mx, off);
+    o.bad = __shfl_down_sync(0xFFFFFFFFu, a.bad, off);
+    o.sum = __shfl_down_sync(0xFFFFFFFFu, a.sum, off);
+    acc_merge(a, o);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) s[warp] = a;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+    a = lane < nw ? s[lane] : Acc{0.0f, 0, 0.0};
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      Acc o;
+      o.mx = __shfl_down_sync(0xFFFFFFFFu, a.mx, off);
+      o.bad = __shfl_down_sync(0xFFFFFFFFu, a.bad, off);
+      o.sum = __shfl_down_sync(0xFFFFFFFFu, a.sum, off);
+      acc_merge(a, o);
+    }
+  }
+  return a;
+}
+
+// One partial per CTA.  LIKELIHOOD: src is state row 0 and the weight
+// w = exp(-(x - y)^2 / 2) is written to w_out before it is reduced.
+template <bool LIKELIHOOD>
+__global__ void __launch_bounds__(kReduceThreads)
+partials_kernel(const float* __restrict__ src, uint32_t n, float y,
+                float* __restrict__ w_out, Partial* __restrict__ parts) {
+  Acc a{0.0f, 0, 0.0};
+  const uint32_t stride = gridDim.x * blockDim.x;
+  const uint32_t t0 = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool vec = ((reinterpret_cast<uintptr_t>(src) & 15u) == 0u) &&
+                   (!LIKELIHOOD || ((reinterpret_cast<uintptr_t>(w_out) & 15u) == 0u));
+  uint32_t tail = 0u;
+  if (vec) {
+    const uint32_t n4 = n / 4u;
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    for (uint32_t t = t0; t < n4; t += stride) {
+      float4 v = __ldg(s4 + t);
+      if constexpr (LIKELIHOOD) {
+        float d;
+        d = v.x - y; v.x = expf(-0.5f * d * d);
+        d = v.y - y; v.y = expf(-0.5f * d * d);
+        d = v.z - y; v.z = expf(-0.5f * d * d);
+        d = v.w - y; v.w = expf(-0.5f * d * d);
+        reinterpret_cast<float4*>(w_out)[t] = v;
+      }
+      acc_add(a, v.x);
+      acc_add(a, v.y);
+      acc_add(a, v.z);
+      acc_add(a, v.w);
+    }
+    tail = n4 * 4u;
+  }
+  for (uint32_t i = tail + t0; i < n; i += stride) {
+    float v = __ldg(src + i);
+    if constexpr (LIKELIHOOD) {
+      const float d = v - y;
+      v = expf(-0.5f * d * d);
+      w_out[i] = v;
+    }
+    acc_add(a, v);
+  }
+  a = block_reduce(a);
+  if (threadIdx.x == 0) parts[blockIdx.x] = Partial{a.mx, a.bad, a.sum};
+}
+
+__global__ void __launch_bounds__(kReduceThreads)
+finalize_kernel(const Partial* __restrict__ parts, int nparts, uint32_t n, double eps,
+                int32_t b_max, int32_t* __restrict__ d_B, int32_t* __restrict__ d_status,
+                double* __restrict__ d_q) {
+  Acc a{0.0f, 0, 0.0};
+  for (int t = threadIdx.x; t < nparts; t += blockDim.x) {
+    const Partial p = parts[t];
+    acc_merge(a, Acc{p.mx, p.bad, p.sum});
+  }
+  a = block_reduce(a);
+  if (threadIdx.x != 0) return;
+  int32_t B = -1, status = kStatusWeights;
+  double q = __longlong_as_double(0x7FF8000000000000LL);  // NaN
+  if (!a.bad && a.mx > 0.0f) {
+    const double r = (a.sum / static_cast<double>(n)) / static_cast<double>(a.mx);
+    q = (r >= 1.0) ? 0.0 : log(eps) / log1p(-r);
+    double c = ceil(q);
+    if (c < 0.0) c = 0.0;
+    if (c <= static_cast<double>(b_max)) {
+      B = static_cast<int32_t>(c);
+      status = 0;
+    }
+  }
+  *d_B = B;
+  *d_status = status;
+  if (d_q) *d_q = q;
+}
+
+// Read `n16` 16-byte words `reps` times; CTAs stride through the buffer
+// so each pass is one coalesced sweep.
+__global__ void __launch_bounds__(512)
+probe_read_kernel(const float4* __restrict__ buf, size_t n16, int reps,
+                  float* __restrict__ sink) {
+  float acc = 0.0f;
+  const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
+  for (int r = 0; r < reps; ++r) {
+    for (size_t t = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < n16;
+         t += stride) {
+      const float4 v = __ldcg(buf + t);
+      acc += (v.x + v.y) + (v.z + v.w);
+    }
+  }
+  // Practically never true; keeps the loads alive.
+  if (acc == 1.2345678e-30f) sink[blockIdx.x] = acc;
+}
+
+}  // namespace
+
+int reduce_grid(uint32_t n) {
+  const uint32_t per_cta = kReduceThreads * 8u;
+  uint32_t g = (n + per_cta - 1u) / per_cta;
+  if (g < 1u) g = 1u;
+  if (g > static_cast<uint32_t>(kMaxParts)) g = kMaxParts;
+  return static_cast<int>(g);
+}
+
+cudaError_t launch_partials(const float* src, uint32_t n, bool likelihood, float y,
+                            float* w_out, Partial* parts, int grid, cudaStream_t st) {
+  if (likelihood) {
+    partials_kernel<true><<<grid, kReduceThreads, 0, st>>>(src, n, y, w_out, parts);
+  } else {
+    partials_kernel<false><<<grid, kReduceThreads, 0, st>>>(src, n, y, w_out, parts);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const Partial* parts, int nparts, uint32_t n, double eps,
+                            int32_t b_max, int32_t* d_B, int32_t* d_status, double* d_q,
+                            cudaStream_t st) {
+  finalize_kernel<<<1, kReduceThreads, 0, st>>>(parts, nparts, n, eps, b_max, d_B,
+                                                d_status, d_q);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_probe_read(const void* buf, size_t bytes, int reps, float* sink,
+                              int grid, cudaStream_t st) {
+  probe_read_kernel<<<grid, 512, 0, st>>>(reinterpret_cast<const float4*>(buf), bytes / 16u,
+                                          reps, sink);
+  return cudaGetLastError();
+}
+
+}  // namespace mego

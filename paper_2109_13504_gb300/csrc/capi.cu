@@ -1,0 +1,403 @@
+// capi.cu -- the extern "C" entry points of libmegopolis.so.
+//
+// Host side only: argument validation, launch-shape selection (memory path,
+// particles per thread, grid sized to the SM count times resident CTAs) and
+// kernel launches on the caller's stream.  No device allocation.
+#include <atomic>
+#include <chrono>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <tuple>
+#include <utility>
+
+#include <cuda_runtime.h>
+
+#include "../../include/megopolis.h"
+#include "bound.cuh"
+#include "resample_kernels.cuh"
+
+namespace {
+
+std::atomic<uint64_t> g_launches{0};
+
+struct DevInfo {
+  int sms = 0;
+  int smem_optin = 0;
+};
+
+bool dev_info(DevInfo* out) {
+  static std::mutex mu;
+  static std::map<int, DevInfo> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(dev);
+  if (it == cache.end()) {
+    DevInfo d;
+    if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return false;
+    if (cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+        cudaSuccess)
+      return false;
+    it = cache.emplace(dev, d).first;
+  }
+  *out = it->second;
+  return true;
+}
+
+int occupancy(const void* kernel, int threads, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, const void*, int, size_t>, int> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const auto key = std::make_tuple(dev, kernel, threads, smem);
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int occ = 0;
+  if (smem > 0 && mego::enable_large_smem(kernel) != cudaSuccess) {
+    cache.emplace(key, 0);
+    return 0;
+  }
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    occ = 0;
+  }
+  cache.emplace(key, occ);
+  return occ;
+}
+
+bool overlaps(const void* a, size_t la, const void* b, size_t lb) {
+  if (!a || !b || la == 0 || lb == 0) return false;
+  const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+  return x < y + lb && y < x + la;
+}
+
+const void* kernel_ptr(int variant, int ppt, bool smem, int gather) {
+  switch (variant) {
+    case MEGO_MEGOPOLIS: return mego::resample_kernel_ptr<mego::kMegopolis>(ppt, smem, gather);
+    case MEGO_METROPOLIS: return mego::resample_kernel_ptr<mego::kMetropolis>(ppt, smem, gather);
+    case MEGO_METROPOLIS_C1: return mego::resample_kernel_ptr<mego::kC1>(ppt, smem, gather);
+    case MEGO_METROPOLIS_C2: return mego::resample_kernel_ptr<mego::kC2>(ppt, smem, gather);
+    default: return nullptr;
+  }
+}
+
+cudaError_t launch_variant(int variant, const mego::LaunchShape& s, int gather,
+                           const mego::ResampleArgs& a, cudaStream_t st) {
+  switch (variant) {
+    case MEGO_MEGOPOLIS: return mego::launch_resample<mego::kMegopolis>(s, gather, a, st);
+    case MEGO_METROPOLIS: return mego::launch_resample<mego::kMetropolis>(s, gather, a, st);
+    case MEGO_METROPOLIS_C1: return mego::launch_resample<mego::kC1>(s, gather, a, st);
+    case MEGO_METROPOLIS_C2: return mego::launch_resample<mego::kC2>(s, gather, a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// Default shape: shared-memory path for small n (the whole vector fits
+// comfortably next to other CTAs), more particles per thread as n grows.
+mego_status choose_shape(int variant, uint32_t n, int gather, const mego_launch_cfg* cfg,
+                         mego::LaunchShape* out) {
+  DevInfo di;
+  if (!dev_info(&di)) return MEGO_ECUDA;
+  const uint32_t nseg = (n + 31u) / 32u;
+  int threads = (cfg && cfg->threads) ? cfg->threads : 256;
+  if (threads < 64 || threads > 256 || threads % 32) return MEGO_EINVAL;
+  int ppt = (cfg && cfg->ppt) ? cfg->ppt : 0;
+  if (ppt == 0) {
+    const uint64_t seg_per_sm = nseg / static_cast<uint64_t>(di.sms);
+    ppt = seg_per_sm >= 256 ? 4 : (seg_per_sm >= 64 ? 2 : 1);
+  }
+  if (ppt != 1 && ppt != 2 && ppt != 4) return MEGO_EINVAL;
+  const size_t w_bytes = (static_cast<size_t>(n) * 4u + 15u) & ~static_cast<size_t>(15u);
+  int path = (cfg && cfg->path) ? cfg->path : MEGO_PATH_AUTO;
+  if (path == MEGO_PATH_AUTO)
+    path = (w_bytes <= 96u * 1024u) ? MEGO_PATH_SMEM : MEGO_PATH_GLOBAL;
+  if (path != MEGO_PATH_SMEM && path != MEGO_PATH_GLOBAL) return MEGO_EINVAL;
+  const bool smem = path == MEGO_PATH_SMEM;
+  if (smem && w_bytes + 1024u > static_cast<size_t>(di.smem_optin)) return MEGO_EINVAL;
+  const size_t smem_bytes = smem ? w_bytes : 0u;
+  const void* kp = kernel_ptr(variant, ppt, smem, gather);
+  if (!kp) return MEGO_EINVAL;
+  int occ = occupancy(kp, threads, smem_bytes);
+  if (occ < 1) return MEGO_EINVAL;
+  if (cfg && cfg->ctas_per_sm > 0 && cfg->ctas_per_sm < occ) occ = cfg->ctas_per_sm;
+  const uint64_t warps_needed = (nseg + ppt - 1u) / static_cast<uint64_t>(ppt);
+  const uint64_t wpc = static_cast<uint64_t>(threads / 32);
+  uint64_t grid = static_cast<uint64_t>(di.sms) * occ;
+  const uint64_t ctas_needed = (warps_needed + wpc - 1u) / wpc;
+  if (grid > ctas_needed) grid = ctas_needed;
+  if (grid < 1u) grid = 1u;
+  out->threads = threads;
+  out->ppt = ppt;
+  out->smem = smem;
+  out->grid = static_cast<int>(grid);
+  out->smem_bytes = smem_bytes;
+  return MEGO_OK;
+}
+
+mego_status check_partition(int variant, uint32_t n, uint32_t psize, uint32_t* nw,
+                            uint32_t* npart) {
+  *nw = 1u;
+  *npart = n;
+  if (variant != MEGO_METROPOLIS_C1 && variant != MEGO_METROPOLIS_C2) return MEGO_OK;
+  if (psize < 4u || psize % 4u) return MEGO_EINVAL;
+  *nw = psize / 4u;
+  if (n % *nw) return MEGO_EINVAL;
+  *npart = n / *nw;
+  return MEGO_OK;
+}
+
+}  // namespace
+
+namespace mego {
+
+cudaError_t enable_large_smem(const void* kernel) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, cudaError_t> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  const auto key = std::make_pair(dev, kernel);
+  auto it = done.find(key);
+  if (it != done.end()) return it->second;
+  int optin = 0;
+  cudaFuncAttributes attr;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&attr, kernel);
+  if (e == cudaSuccess) {
+    const int dyn = optin - static_cast<int>(attr.sharedSizeBytes);
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+  }
+  if (e != cudaSuccess) cudaGetLastError();  // do not leave the error pending
+  done.emplace(key, e);
+  return e;
+}
+
+}  // namespace mego
+
+extern "C" {
+
+int mego_abi_version(void) { return MEGO_ABI_VERSION; }
+
+const char* mego_status_string(int status) {
+  switch (status) {
+    case MEGO_OK: return "ok";
+    case MEGO_EINVAL: return "invalid argument";
+    case MEGO_ENOMEM: return "workspace too small";
+    case MEGO_ECUDA: return "CUDA runtime error";
+    case MEGO_ETIMEOUT: return "timed out waiting for the stream";
+    case MEGO_EWEIGHTS: return "invalid weights or bound above its cap";
+    default: return "unknown status";
+  }
+}
+
+uint64_t mego_launch_count(void) { return g_launches.load(); }
+
+size_t mego_workspace_bytes(int32_t n) {
+  (void)n;
+  return static_cast<size_t>(mego::kMaxParts) * sizeof(mego::Partial) + 256u;
+}
+
+mego_status mego_resample_gather(const float* d_w, int32_t n, int32_t B, const int32_t* d_B,
+                                 uint64_t seed, uint32_t stream_id, int variant,
+                                 uint32_t psize_bytes, const float* d_x_in, float* d_x_out,
+                                 int32_t dim, int64_t ld, int layout, int32_t* d_anc,
+                                 const mego_launch_cfg* cfg, void* stream) {
+  if (!d_w || n < 1 || n > MEGO_N_MAX) return MEGO_EINVAL;
+  if (!d_B && (B < 0 || B > MEGO_B_MAX)) return MEGO_EINVAL;
+  if (variant < MEGO_MEGOPOLIS || variant > MEGO_METROPOLIS_C2) return MEGO_EINVAL;
+  const uint32_t un = static_cast<uint32_t>(n);
+  uint32_t nw = 1u, npart = un;
+  if (check_partition(variant, un, psize_bytes, &nw, &npart) != MEGO_OK) return MEGO_EINVAL;
+  int gather = mego::kGatherNone;
+  size_t x_bytes = 0;
+  if (d_x_in || d_x_out) {
+    if (!d_x_in || !d_x_out) return MEGO_EINVAL;
+    if (layout == MEGO_LAYOUT_SOA) {
+      if (dim < 1 || ld < n) return MEGO_EINVAL;
+      gather = mego::kGatherSoa;
+      x_bytes = (static_cast<size_t>(dim - 1) * static_cast<size_t>(ld) + un) * 4u;
+    } else if (layout == MEGO_LAYOUT_AOS4) {
+      if (dim != 4) return MEGO_EINVAL;
+      if ((reinterpret_cast<uintptr_t>(d_x_in) | reinterpret_cast<uintptr_t>(d_x_out)) & 15u)
+        return MEGO_EINVAL;
+      gather = mego::kGatherAos4;
+      x_bytes = static_cast<size_t>(un) * 16u;
+    } else {
+      return MEGO_EINVAL;
+    }
+    if (overlaps(d_x_in, x_bytes, d_x_out, x_bytes)) return MEGO_EINVAL;
+  } else if (!d_anc) {
+    return MEGO_EINVAL;  // nothing to write
+  }
+  const size_t w_bytes = static_cast<size_t>(un) * 4u;
+  if (d_anc && overlaps(d_anc, w_bytes, d_w, w_bytes)) return MEGO_EINVAL;
+  if (d_anc && d_x_out && overlaps(d_anc, w_bytes, d_x_out, x_bytes)) return MEGO_EINVAL;
+  if (d_x_out && overlaps(d_x_out, x_bytes, d_w, w_bytes)) return MEGO_EINVAL;
+
+  mego::LaunchShape shape;
+  mego_status st = choose_shape(variant, un, gather, cfg, &shape);
+  if (st != MEGO_OK) return st;
+
+  mego::ResampleArgs a;
+  std::memset(&a, 0, sizeof a);
+  a.w = d_w;
+  a.B_dev = d_B;
+  a.anc = d_anc;
+  a.x_in = d_x_in;
+  a.x_out = d_x_out;
+  a.fault = nullptr;
+  a.ld = ld;
+  a.n = un;
+  a.nseg = (un + 31u) / 32u;
+  a.B = d_B ? 0 : B;
+  a.k0 = static_cast<uint32_t>(seed & 0xFFFFFFFFull);
+  a.k1 = static_cast<uint32_t>(seed >> 32);
+  a.sid = stream_id;
+  a.dim = dim;
+  a.nw = nw;
+  a.npart = npart;
+  const cudaError_t e =
+      launch_variant(variant, shape, gather, a, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return MEGO_ECUDA;
+  g_launches.fetch_add(1);
+  return MEGO_OK;
+}
+
+mego_status mego_resample(const float* d_w, int32_t n, int32_t B, uint64_t seed,
+                          uint32_t stream_id, int variant, int32_t* d_anc, void* stream) {
+  if (!d_anc) return MEGO_EINVAL;
+  if (variant != MEGO_MEGOPOLIS && variant != MEGO_METROPOLIS) return MEGO_EINVAL;
+  return mego_resample_gather(d_w, n, B, nullptr, seed, stream_id, variant, 0u, nullptr,
+                              nullptr, 0, 0, MEGO_LAYOUT_SOA, d_anc, nullptr, stream);
+}
+
+static mego_status bound_common(const float* src, int32_t n, bool likelihood, float y,
+                                double eps, int32_t b_max, float* d_w, int32_t* d_B,
+                                int32_t* d_status, double* d_q, void* d_ws, size_t ws_bytes,
+                                void* stream) {
+  if (!src || !d_B || !d_status || !d_ws) return MEGO_EINVAL;
+  if (likelihood && !d_w) return MEGO_EINVAL;
+  if (n < 1 || n > MEGO_N_MAX) return MEGO_EINVAL;
+  if (!(eps > 0.0 && eps <= 1.0)) return MEGO_EINVAL;
+  if (b_max < 1 || b_max > MEGO_B_MAX) return MEGO_EINVAL;
+  if (ws_bytes < mego_workspace_bytes(n)) return MEGO_ENOMEM;
+  if (reinterpret_cast<uintptr_t>(d_ws) & 255u) return MEGO_EINVAL;
+  const uint32_t un = static_cast<uint32_t>(n);
+  if (likelihood && overlaps(src, un * 4u, d_w, un * 4u)) return MEGO_EINVAL;
+  auto* parts = static_cast<mego::Partial*>(d_ws);
+  const int grid = mego::reduce_grid(un);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (mego::launch_partials(src, un, likelihood, y, d_w, parts, grid, st) != cudaSuccess)
+    return MEGO_ECUDA;
+  g_launches.fetch_add(1);
+  if (mego::launch_finalize(parts, grid, un, eps, b_max, d_B, d_status, d_q, st) !=
+      cudaSuccess)
+    return MEGO_ECUDA;
+  g_launches.fetch_add(1);
+  return MEGO_OK;
+}
+
+mego_status mego_compute_B(const float* d_w, int32_t n, double eps, int32_t b_max,
+                           int32_t* d_B, int32_t* d_status, double* d_q, void* d_ws,
+                           size_t ws_bytes, void* stream) {
+  return bound_common(d_w, n, false, 0.0f, eps, b_max, nullptr, d_B, d_status, d_q, d_ws,
+                      ws_bytes, stream);
+}
+
+mego_status mego_likelihood_B(const float* d_x, int32_t n, float y, double eps, int32_t b_max,
+                              float* d_w, int32_t* d_B, int32_t* d_status, double* d_q,
+                              void* d_ws, size_t ws_bytes, void* stream) {
+  return bound_common(d_x, n, true, y, eps, b_max, d_w, d_B, d_status, d_q, d_ws, ws_bytes,
+                      stream);
+}
+
+mego_status mego_sync_status(const int32_t* d_status, void* stream, double timeout_s,
+                             int32_t* h_status) {
+  if (!d_status || !h_status || !(timeout_s >= 0.0)) return MEGO_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEvent_t ev;
+  if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return MEGO_ECUDA;
+  if (cudaEventRecord(ev, st) != cudaSuccess) {
+    cudaEventDestroy(ev);
+    return MEGO_ECUDA;
+  }
+  const auto deadline = std::chrono::steady_clock::now() +
+                        std::chrono::duration_cast<std::chrono::steady_clock::duration>(
+                            std::chrono::duration<double>(timeout_s));
+  for (;;) {
+    const cudaError_t q = cudaEventQuery(ev);
+    if (q == cudaSuccess) break;
+    if (q != cudaErrorNotReady) {
+      cudaEventDestroy(ev);
+      return MEGO_ECUDA;
+    }
+    if (std::chrono::steady_clock::now() >= deadline) {
+      cudaEventDestroy(ev);
+      return MEGO_ETIMEOUT;
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+  cudaEventDestroy(ev);
+  int32_t v = 0;
+  if (cudaMemcpy(&v, d_status, sizeof v, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return MEGO_ECUDA;
+  *h_status = v;
+  return MEGO_OK;
+}
+
+mego_status mego_resample_host(const float* h_w, int32_t n, int32_t B, double eps,
+                               uint64_t seed, uint32_t stream_id, int variant, int32_t* h_anc,
+                               int32_t* h_B, float* d_w, int32_t* d_anc, void* d_scalars,
+                               void* d_ws, size_t ws_bytes, void* stream) {
+  if (!h_w || !h_anc || !d_w || !d_anc || !d_scalars) return MEGO_EINVAL;
+  if (n < 1 || n > MEGO_N_MAX || B > MEGO_B_MAX) return MEGO_EINVAL;
+  if (variant != MEGO_MEGOPOLIS && variant != MEGO_METROPOLIS) return MEGO_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t bytes = static_cast<size_t>(n) * 4u;
+  int32_t* d_Bp = static_cast<int32_t*>(d_scalars);
+  int32_t* d_status = d_Bp + 1;
+  double* d_q = reinterpret_cast<double*>(static_cast<char*>(d_scalars) + 8);
+  if (cudaMemcpyAsync(d_w, h_w, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return MEGO_ECUDA;
+  mego_status s;
+  if (B < 0) {
+    s = mego_compute_B(d_w, n, eps, MEGO_B_MAX, d_Bp, d_status, d_q, d_ws, ws_bytes, stream);
+    if (s != MEGO_OK) return s;
+    s = mego_resample_gather(d_w, n, 0, d_Bp, seed, stream_id, variant, 0u, nullptr, nullptr,
+                             0, 0, MEGO_LAYOUT_SOA, d_anc, nullptr, stream);
+  } else {
+    s = mego_resample_gather(d_w, n, B, nullptr, seed, stream_id, variant, 0u, nullptr,
+                             nullptr, 0, 0, MEGO_LAYOUT_SOA, d_anc, nullptr, stream);
+  }
+  if (s != MEGO_OK) return s;
+  if (cudaMemcpyAsync(h_anc, d_anc, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return MEGO_ECUDA;
+  int32_t hb[2] = {B, 0};
+  if (B < 0 &&
+      cudaMemcpyAsync(hb, d_Bp, sizeof hb, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return MEGO_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return MEGO_ECUDA;
+  if (h_B) *h_B = hb[0];
+  return hb[1] == 0 ? MEGO_OK : MEGO_EWEIGHTS;
+}
+
+mego_status mego_probe_read(const void* d_buf, size_t bytes, int32_t reps, float* d_sink,
+                            void* stream) {
+  if (!d_buf || !d_sink || bytes < 16u || bytes % 16u || reps < 1) return MEGO_EINVAL;
+  if (reinterpret_cast<uintptr_t>(d_buf) & 15u) return MEGO_EINVAL;
+  DevInfo di;
+  if (!dev_info(&di)) return MEGO_ECUDA;
+  if (mego::launch_probe_read(d_buf, bytes, reps, d_sink, di.sms * 4,
+                              static_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return MEGO_ECUDA;
+  g_launches.fetch_add(1);
+  return MEGO_OK;
+}
+
+}  // extern "C"

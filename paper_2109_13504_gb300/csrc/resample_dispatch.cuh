@@ -1,0 +1,82 @@
+// resample_dispatch.cuh -- instantiates resample_kernel for one variant over
+// (particles per thread, weight path, gather layout) and launches it.
+// Included once per variant translation unit, with MEGO_VARIANT defined.
+#pragma once
+
+#include "resample_kernels.cuh"
+
+namespace mego {
+namespace {
+
+template <int V, int P, bool S, int G>
+cudaError_t launch_one(const LaunchShape& s, const ResampleArgs& a, cudaStream_t st) {
+  auto* k = &resample_kernel<V, P, S, G>;
+  if (S) {
+    const cudaError_t e = enable_large_smem(reinterpret_cast<const void*>(k));
+    if (e != cudaSuccess) return e;
+  }
+  k<<<s.grid, s.threads, s.smem_bytes, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int V, int P, bool S, int G>
+const void* ptr_one() {
+  return reinterpret_cast<const void*>(&resample_kernel<V, P, S, G>);
+}
+
+template <int V, bool S, int G>
+cudaError_t by_ppt(const LaunchShape& s, const ResampleArgs& a, cudaStream_t st) {
+  switch (s.ppt) {
+    case 1: return launch_one<V, 1, S, G>(s, a, st);
+    case 2: return launch_one<V, 2, S, G>(s, a, st);
+    case 4: return launch_one<V, 4, S, G>(s, a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int V, bool S, int G>
+const void* ptr_by_ppt(int ppt) {
+  switch (ppt) {
+    case 1: return ptr_one<V, 1, S, G>();
+    case 2: return ptr_one<V, 2, S, G>();
+    case 4: return ptr_one<V, 4, S, G>();
+    default: return nullptr;
+  }
+}
+
+template <int V, bool S>
+cudaError_t by_gather(const LaunchShape& s, int gather, const ResampleArgs& a, cudaStream_t st) {
+  switch (gather) {
+    case kGatherNone: return by_ppt<V, S, kGatherNone>(s, a, st);
+    case kGatherSoa: return by_ppt<V, S, kGatherSoa>(s, a, st);
+    case kGatherAos4: return by_ppt<V, S, kGatherAos4>(s, a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int V, bool S>
+const void* ptr_by_gather(int ppt, int gather) {
+  switch (gather) {
+    case kGatherNone: return ptr_by_ppt<V, S, kGatherNone>(ppt);
+    case kGatherSoa: return ptr_by_ppt<V, S, kGatherSoa>(ppt);
+    case kGatherAos4: return ptr_by_ppt<V, S, kGatherAos4>(ppt);
+    default: return nullptr;
+  }
+}
+
+}  // namespace
+
+template <>
+cudaError_t launch_resample<MEGO_VARIANT>(const LaunchShape& s, int gather,
+                                          const ResampleArgs& a, cudaStream_t st) {
+  return s.smem ? by_gather<MEGO_VARIANT, true>(s, gather, a, st)
+                : by_gather<MEGO_VARIANT, false>(s, gather, a, st);
+}
+
+template <>
+const void* resample_kernel_ptr<MEGO_VARIANT>(int ppt, bool smem, int gather) {
+  return smem ? ptr_by_gather<MEGO_VARIANT, true>(ppt, gather)
+              : ptr_by_gather<MEGO_VARIANT, false>(ppt, gather);
+}
+
+}  // namespace mego

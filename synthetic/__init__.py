@@ -60,3 +60,8 @@ def request_stream(count: int, rate_per_s: float, lo_log2: float, hi_log2: float
     t = np.cumsum(gaps)
     sizes = np.floor(2.0 ** g.uniform(lo_log2, hi_log2, int(count))).astype(np.int64)
     return t, sizes
+
+
+def uniform_weights(n: int, seed: int) -> np.ndarray:
+    """w_i ~ U[0, 1) float32 (cheap inputs for the largest sizes)."""
+    return _rng(seed, 0x554E).random(int(n), dtype=np.float32)

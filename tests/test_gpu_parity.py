@@ -1,0 +1,323 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Ancestors and gathered state must be bit-exact (integer/index work and a
+copy).  The bound B must be equal, except when the value before the ceiling
+lies within 1e-9 (relative) of an integer, where the CPU and GPU sums may
+round to different sides; then |B_gpu - B_cpu| <= 1.  The likelihood weight
+(expf on the GPU, exp in double on the CPU) must agree within the bound
+derived in the design doc: |w_gpu - w_ref| <= (4 + 2|a|) 2^-23 w_ref + 2^-149,
+a = (x - y)^2 / 2.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synthetic
+
+pytestmark = pytest.mark.gpu
+
+mego = pytest.importorskip("paper_2109_13504_gb300")
+
+DEV = torch.device("cuda:0")
+VARIANTS = [mego.MEGOPOLIS, mego.METROPOLIS]
+
+
+def _gpu(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def _anc(w_h, B, seed, variant, cfg=None, sid=0, psize=0):
+    w = _gpu(w_h)
+    anc = torch.full((w_h.size,), -7, dtype=torch.int32, device=DEV)
+    mego.mego_resample_gather(w, B, None, seed, sid, variant, psize, anc=anc, cfg=cfg)
+    torch.cuda.synchronize()
+    return anc.cpu().numpy()
+
+
+def _b_equal(B_gpu, B_cpu, q):
+    if B_gpu == B_cpu:
+        return True
+    near = abs(q - round(q)) <= 1e-9 * max(1.0, abs(q))
+    return near and abs(B_gpu - B_cpu) <= 1
+
+
+# ----------------------------------------------------------------------------
+# Config: N = 4096, B = 32, seed 1, both variants, full bit-exact
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_small_config_bit_exact(variant):
+    w_h = synthetic.gaussian_weights(4096, 2.0, 1)
+    ref = oracle.resample(w_h, 32, 1, variant)
+    got = _anc(w_h, 32, 1, variant)
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("path", [mego.PATH_GLOBAL, mego.PATH_SMEM])
+@pytest.mark.parametrize("ppt", [1, 2, 4])
+@pytest.mark.parametrize("threads", [64, 256])
+def test_launch_shape_invariance(variant, path, ppt, threads):
+    n = 4096 + 1000 + 3
+    w_h = synthetic.gaussian_weights(n, 3.0, 2)
+    ref = oracle.resample(w_h, 45, 9, variant)
+    got = _anc(w_h, 45, 9, variant, cfg={"threads": threads, "ppt": ppt, "path": path})
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("n", [1, 2, 5, 31, 32, 33, 64, 100, 1000, 4097, 12345, 70001])
+@pytest.mark.parametrize("B", [0, 1, 7, 33])
+def test_ragged_sizes_bit_exact(variant, n, B):
+    w_h = synthetic.gaussian_weights(n, 1.0, 3 + n)
+    ref = oracle.resample(w_h, B, 5, variant)
+    assert np.array_equal(_anc(w_h, B, 5, variant), ref)
+    if n > 64:
+        ref2 = oracle.resample(w_h, B, 5, variant, stream_id=3)
+        assert np.array_equal(_anc(w_h, B, 5, variant, sid=3), ref2)
+
+
+def test_equal_and_single_weight_cases():
+    n = 5000
+    w_h = np.full(n, 0.5, np.float32)
+    for v in VARIANTS:
+        assert np.array_equal(_anc(w_h, 9, 4, v), oracle.resample(w_h, 9, 4, v))
+    w_h = np.zeros(n, np.float32)
+    w_h[1234] = 1.0
+    for v in VARIANTS:
+        got = _anc(w_h, 2000, 4, v)
+        assert got[1234] == 1234
+        assert np.array_equal(got, oracle.resample(w_h, 2000, 4, v))
+
+
+# ----------------------------------------------------------------------------
+# Scaling sweep: N = 2^14..2^24, y = 0..4, 5 seeds, B from Eq. 3 at eps 0.01
+
+
+def _sample_idx(n, rng, count=600):
+    idx = set(range(min(n, 96)))
+    idx.update(range(max(0, n - 96), n))
+    idx.update(rng.integers(0, n, count).tolist())
+    return np.array(sorted(idx), dtype=np.int64)
+
+
+@pytest.mark.parametrize("log2n", [14, 16, 18, 20, 22, 24])
+def test_scaling_sweep_sampled(log2n):
+    n = 1 << log2n
+    rng = np.random.default_rng(log2n)
+    ws = torch.empty(mego.workspace_bytes(n), dtype=torch.uint8, device=DEV)
+    anc = torch.empty(n, dtype=torch.int32, device=DEV)
+    for y in range(5):
+        for dseed in range(1, 6):
+            w_h = synthetic.gaussian_weights(n, y, dseed)
+            w = _gpu(w_h)
+            B_dev, status, q_dev = mego.mego_compute_B(w, 0.01, ws=ws)
+            st, B_cpu, q_cpu = oracle.compute_B(w_h, 0.01)
+            assert st == oracle.OK
+            assert mego.mego_sync_status(status) == mego.MEGO_OK
+            B_gpu = int(B_dev.item())
+            assert _b_equal(B_gpu, B_cpu, q_cpu), (n, y, dseed, B_gpu, B_cpu, q_cpu)
+            assert abs(float(q_dev.item()) - q_cpu) <= 1e-9 * max(1.0, q_cpu)
+            full = n <= (1 << 14)
+            idx = None if full else _sample_idx(n, rng)
+            for v in VARIANTS:
+                mego.mego_resample_gather(w, 0, B_dev, 100 + dseed, 0, v, anc=anc)
+                got = anc.cpu().numpy()
+                if full:
+                    ref = oracle.resample(w_h, B_gpu, 100 + dseed, v)
+                    assert np.array_equal(got, ref), (n, y, dseed, v)
+                else:
+                    ref = oracle.resample_at(w_h, B_gpu, 100 + dseed, idx, v)
+                    assert np.array_equal(got[idx], ref), (n, y, dseed, v)
+                    assert got.min() >= 0 and got.max() < n
+
+
+def test_maximum_size_sampled():
+    n = mego.N_MAX
+    try:
+        w = torch.empty(n, dtype=torch.float32, device=DEV)
+        anc = torch.empty(n, dtype=torch.int32, device=DEV)
+    except RuntimeError:
+        pytest.skip("not enough device memory for N_MAX")
+    w_h = synthetic.uniform_weights(n, 77)
+    w.copy_(torch.from_numpy(w_h))
+    rng = np.random.default_rng(0)
+    idx = _sample_idx(n, rng, 300)
+    for v in VARIANTS:
+        mego.mego_resample_gather(w, 3, None, 11, 0, v, anc=anc)
+        got = anc[torch.from_numpy(idx).to(DEV)].cpu().numpy()
+        assert np.array_equal(got, oracle.resample_at(w_h, 3, 11, idx, v))
+    del w, anc
+    torch.cuda.empty_cache()
+
+
+# ----------------------------------------------------------------------------
+# Gather, device-side bound, likelihood
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("n", [777, 4096, 100003])
+def test_gather_soa_and_aos4(variant, n):
+    w_h = synthetic.gaussian_weights(n, 2.0, 4)
+    x_h = synthetic.gaussian_state(n, 6, 5)
+    ref = oracle.resample(w_h, 16, 3, variant)
+    w = _gpu(w_h)
+    # SoA with a row stride larger than n
+    ld = n + 13
+    x_pad = np.zeros((6, ld), np.float32)
+    x_pad[:, :n] = x_h
+    x_in = _gpu(x_pad)
+    x_out = torch.full_like(x_in, -1.0)
+    anc = torch.empty(n, dtype=torch.int32, device=DEV)
+    mego.mego_resample_gather(w, 16, None, 3, 0, variant, x_in=x_in, x_out=x_out, anc=anc)
+    out = x_out.cpu().numpy()
+    assert np.array_equal(anc.cpu().numpy(), ref)
+    assert np.array_equal(out[:, :n], oracle.gather_soa(x_h, ref))
+    assert (out[:, n:] == -1.0).all()          # padding untouched
+    # AoS4, ancestors not requested
+    a_h = np.ascontiguousarray(x_h[:4].T)
+    a_in = _gpu(a_h)
+    a_out = torch.empty_like(a_in)
+    mego.mego_resample_gather(w, 16, None, 3, 0, variant, x_in=a_in, x_out=a_out,
+                              layout=mego.LAYOUT_AOS4)
+    assert np.array_equal(a_out.cpu().numpy(), oracle.gather_aos4(a_h, ref))
+
+
+def test_device_bound_path_equals_host_path():
+    n = 1 << 18
+    w_h = synthetic.gaussian_weights(n, 3.0, 9)
+    w = _gpu(w_h)
+    B_dev, status, _ = mego.mego_compute_B(w, 0.01)
+    a1 = torch.empty(n, dtype=torch.int32, device=DEV)
+    mego.mego_resample_gather(w, 0, B_dev, 5, 0, mego.MEGOPOLIS, anc=a1)
+    B = int(B_dev.item())
+    a2 = mego.mego_resample(w, B, 5)
+    assert torch.equal(a1, a2)
+    assert torch.equal(mego.resample(w, None, 0.01, 5), a2)
+
+
+def test_likelihood_weights_and_fused_step():
+    n = (1 << 20) + 5
+    x_h = synthetic.gaussian_state(n, 6, 12)
+    x = _gpu(x_h)
+    w, B_dev, status, q = mego.mego_likelihood_B(x[0], 2.0, 0.01)
+    x_out = torch.empty_like(x)
+    anc = torch.empty(n, dtype=torch.int32, device=DEV)
+    mego.mego_resample_gather(w, 0, B_dev, 21, 0, mego.MEGOPOLIS, x_in=x, x_out=x_out,
+                              anc=anc)
+    assert mego.mego_sync_status(status) == mego.MEGO_OK
+    w_gpu = w.cpu().numpy()
+    ref = np.exp(-0.5 * (x_h[0].astype(np.float64) - 2.0) ** 2)
+    a = 0.5 * (x_h[0].astype(np.float64) - 2.0) ** 2
+    tol = (4.0 + 2.0 * a) * 2.0 ** -23 * ref + 2.0 ** -149
+    assert (np.abs(w_gpu.astype(np.float64) - ref) <= tol).all()
+    # The bound and the ancestors are then exact functions of the GPU weights.
+    st, B_cpu, q_cpu = oracle.compute_B(w_gpu, 0.01)
+    assert _b_equal(int(B_dev.item()), B_cpu, q_cpu)
+    B = int(B_dev.item())
+    idx = _sample_idx(n, np.random.default_rng(1))
+    got = anc.cpu().numpy()
+    assert np.array_equal(got[idx], oracle.resample_at(w_gpu, B, 21, idx, mego.MEGOPOLIS))
+    out = x_out.cpu().numpy()
+    assert np.array_equal(out[:, idx], x_h[:, got[idx]])
+
+
+# ----------------------------------------------------------------------------
+# Errors and status
+
+
+def test_invalid_weights_report_status_and_write_nothing():
+    n = 3000
+    for bad in (np.nan, np.inf, -1.0):
+        w_h = synthetic.gaussian_weights(n, 1.0, 2)
+        w_h[17] = bad
+        w = _gpu(w_h)
+        B_dev, status, _ = mego.mego_compute_B(w, 0.01)
+        anc = torch.full((n,), -5, dtype=torch.int32, device=DEV)
+        mego.mego_resample_gather(w, 0, B_dev, 1, 0, mego.MEGOPOLIS, anc=anc)
+        assert mego.mego_sync_status(status) == mego.MEGO_EWEIGHTS
+        assert int(B_dev.item()) == -1
+        assert (anc.cpu().numpy() == -5).all()
+    w = torch.zeros(n, dtype=torch.float32, device=DEV)
+    B_dev, status, _ = mego.mego_compute_B(w, 0.01)
+    assert mego.mego_sync_status(status) == mego.MEGO_EWEIGHTS
+    # a bound above its cap
+    w_h = np.zeros(1 << 16, np.float32)
+    w_h[0] = 1.0
+    B_dev, status, _ = mego.mego_compute_B(_gpu(w_h), 0.01, b_max=100)
+    assert mego.mego_sync_status(status) == mego.MEGO_EWEIGHTS
+
+
+def test_argument_errors():
+    w = torch.ones(100, dtype=torch.float32, device=DEV)
+    anc = torch.empty(100, dtype=torch.int32, device=DEV)
+    with pytest.raises(mego.MegoError):
+        mego.mego_resample(w, -1, 1, anc=anc)
+    with pytest.raises(mego.MegoError):
+        mego.mego_resample_gather(w, 4, None, 1, 0, mego.METROPOLIS_C1, psize_bytes=12,
+                                  anc=anc)   # 3 weights per partition does not divide 100
+    with pytest.raises(mego.MegoError):
+        mego.mego_resample_gather(w, 4, None, 1, 0, mego.MEGOPOLIS, anc=anc,
+                                  cfg={"threads": 48})
+    with pytest.raises(mego.MegoError):
+        mego.mego_compute_B(w, 0.0)
+    with pytest.raises(mego.MegoError):
+        mego.mego_compute_B(w, 0.01, ws=torch.empty(16, dtype=torch.uint8, device=DEV))
+    big = torch.ones(100_000, dtype=torch.float32, device=DEV)
+    with pytest.raises(mego.MegoError):      # 400 KB does not fit shared memory
+        mego.mego_resample_gather(big, 4, None, 1, 0, mego.MEGOPOLIS,
+                                  anc=torch.empty(100_000, dtype=torch.int32, device=DEV),
+                                  cfg={"path": mego.PATH_SMEM})
+
+
+def test_sync_status_deadline():
+    # A long resample and a zero deadline: the wait gives up, the stream
+    # keeps running, and a later wait succeeds.
+    n = 1 << 22
+    w = torch.rand(n, dtype=torch.float32, device=DEV)
+    anc = torch.empty(n, dtype=torch.int32, device=DEV)
+    status = torch.zeros(1, dtype=torch.int32, device=DEV)
+    torch.cuda.synchronize()
+    mego.mego_resample_gather(w, 4000, None, 1, 0, mego.METROPOLIS, anc=anc)
+    with pytest.raises(mego.MegoError) as ei:
+        mego.mego_sync_status(status, timeout_s=0.0)
+    assert ei.value.status == mego.MEGO_ETIMEOUT
+    assert mego.mego_sync_status(status, timeout_s=60.0) == mego.MEGO_OK
+
+
+# ----------------------------------------------------------------------------
+# End-to-end on host buffers, and Metropolis-C1/C2
+
+
+def test_host_buffer_call_matches_device_call():
+    n = 100_000
+    w_h = synthetic.gaussian_weights(n, 2.0, 6)
+    h_w = torch.from_numpy(w_h).pin_memory()
+    h_anc = torch.empty(n, dtype=torch.int32).pin_memory()
+    d_w = torch.empty(n, dtype=torch.float32, device=DEV)
+    d_anc = torch.empty(n, dtype=torch.int32, device=DEV)
+    d_sc = torch.empty(32, dtype=torch.uint8, device=DEV)
+    ws = torch.empty(mego.workspace_bytes(n), dtype=torch.uint8, device=DEV)
+    B = mego.mego_resample_host(h_w, -1, 0.01, 3, 0, mego.MEGOPOLIS, h_anc, d_w, d_anc, d_sc,
+                                ws)
+    st, B_cpu, q = oracle.compute_B(w_h, 0.01)
+    assert _b_equal(B, B_cpu, q)
+    assert np.array_equal(h_anc.numpy(), oracle.resample(w_h, B, 3, mego.MEGOPOLIS))
+    B2 = mego.mego_resample_host(h_w, 7, 0.01, 3, 0, mego.METROPOLIS, h_anc, d_w, d_anc, d_sc,
+                                 ws)
+    assert B2 == 7
+    assert np.array_equal(h_anc.numpy(), oracle.resample(w_h, 7, 3, mego.METROPOLIS))
+
+
+@pytest.mark.parametrize("variant", [mego.METROPOLIS_C1, mego.METROPOLIS_C2])
+@pytest.mark.parametrize("psize", [128, 512, 2048])
+@pytest.mark.parametrize("ppt", [1, 2, 4])
+def test_partition_variants_bit_exact(variant, psize, ppt):
+    n = 1 << 13
+    w_h = synthetic.gaussian_weights(n, 2.0, 7)
+    ref = oracle.resample(w_h, 37, 8, variant, psize_bytes=psize)
+    got = _anc(w_h, 37, 8, variant, cfg={"ppt": ppt}, psize=psize)
+    assert np.array_equal(got, ref)
