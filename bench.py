@@ -1,0 +1,452 @@
+"""Benchmark: resampled particles/s at N = 2^20 (Megopolis vs Metropolis).
+
+Workload ("scaling sweep at N = 2^20"): five weight vectors w_i =
+exp(-(x_i - y)^2 / 2), x_i ~ N(0,1), y = 0..4 (Eq. 12 shape, synthetic),
+resident in HBM.  One step resamples all five: for each y the bound B
+(Eq. 3, eps = 0.01) is computed on the device and the Megopolis kernel
+(Algorithm 5) reads it from device memory and writes int32 ancestors.
+value = 5 * 2^20 * steps / (device time of the steps).
+
+Extra legs on the same inputs: the Metropolis baseline (Algorithm 2) with the
+same bound; the fused step (likelihood of a 6-dim SoA state against y = 2,
+bound, Megopolis, gather of the state); an end-to-end leg through the
+host-buffer C-ABI call (copies inside the timed region); the CPU oracle on a
+bounded sample (the CPU baseline).
+
+Timing: W warm-up steps, then K steps, each bracketed by CUDA events on the
+launching stream; a 256 MiB buffer (> L2) is written between steps, outside
+the events.  Clocks are sampled with nvidia-smi during the timed region.
+Multi-GPU (torchrun): replicas, one per rank, no collective on the data
+path; value sums the particles of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "resampled particles/s at N=2^20 (Megopolis vs Metropolis)"
+UNIT = "particles/s"
+N = 1 << 20
+YS = (0, 1, 2, 3, 4)
+EPS = 0.01
+SEED = 1
+FLUSH_BYTES = 256 << 20
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "megopolis_resample_n2p20_y4.md")
+KERNEL_SOURCES = ("resample_kernels.cuh", "device_common.cuh", "resample_dispatch.cuh",
+                  "resample_megopolis.cu")
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _kernel_hash() -> str:
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2109_13504_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _profiled_traffic():
+    """DRAM bytes per launch of the Megopolis kernel from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
+    try:
+        text = open(PROFILE_TRAFFIC).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)\s*\(kernel source ([0-9a-f]+)\)", text)
+    if not m or m.group(2) != _kernel_hash():
+        return None
+    return float(m.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _cpu_baseline(sample_particles: int):
+    """The CPU oracle, single-threaded, on the first `sample_particles`
+    particles of each of the five weight vectors (Megopolis, same B)."""
+    import oracle
+    import synthetic
+    oracle.build()
+    total_p = 0
+    t_total = 0.0
+    seeds = (SEED, SEED + 1)
+    for y in YS:
+        w = synthetic.gaussian_weights(N, y, SEED + y)
+        for seed in seeds:
+            t0 = time.perf_counter()
+            st, B, _ = oracle.compute_B(w, EPS)
+            oracle.resample(w, B, seed, oracle.MEGOPOLIS, i0=0, i1=sample_particles)
+            t_total += time.perf_counter() - t0
+            total_p += sample_particles
+    return {"value": total_p / t_total, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "first %d of %d particles for each y in 0..4 and 2 resampling "
+                      "seeds (bound over all N, Megopolis chains for the sample); "
+                      "%.1f s of CPU work" % (sample_particles, N, t_total)}
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle as it stands, timed on the host."""
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    import synthetic
+    oracle.build()
+    sample = args.reference_sample
+    ws = [synthetic.gaussian_weights(N, y, SEED + y) for y in YS]
+
+    def step():
+        for w in ws:
+            st, B, _ = oracle.compute_B(w, EPS)
+            oracle.resample(w, B, SEED, oracle.MEGOPOLIS, i0=0, i1=sample)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = sample * len(YS) * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "scaling sweep at N=2^20, y=0..4, eps=0.01, Megopolis; "
+                               "CPU oracle on the first %d particles per y" % sample,
+                   "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "first %d of %d particles per y, %d steps"
+                                   % (sample, N, args.steps)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    import paper_2109_13504_gb300 as mego
+    import synthetic
+
+    world, rank, local = _dist()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    ws_bytes = mego.workspace_bytes(N)
+    w_dev = [torch.from_numpy(synthetic.gaussian_weights(N, y, SEED + y)).to(dev) for y in YS]
+    ws = [torch.empty(ws_bytes, dtype=torch.uint8, device=dev) for _ in YS]
+    B_dev = [torch.empty(1, dtype=torch.int32, device=dev) for _ in YS]
+    st_dev = [torch.empty(1, dtype=torch.int32, device=dev) for _ in YS]
+    q_dev = [torch.empty(1, dtype=torch.float64, device=dev) for _ in YS]
+    anc = [torch.empty(N, dtype=torch.int32, device=dev) for _ in YS]
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step(variant, ev_pairs=None):
+        for t, _ in enumerate(YS):
+            if ev_pairs is not None:
+                ev_pairs[t][0].record(stream)
+            mego.mego_compute_B(w_dev[t], EPS, B_dev=B_dev[t], status=st_dev[t], q=q_dev[t],
+                                ws=ws[t], stream=stream)
+            if ev_pairs is not None and t == len(YS) - 1:
+                ev_pairs[t][2].record(stream)
+            mego.mego_resample_gather(w_dev[t], 0, B_dev[t], SEED, 0, variant, anc=anc[t],
+                                      stream=stream)
+            if ev_pairs is not None:
+                ev_pairs[t][1].record(stream)
+
+    def timed(variant, steps, warmup):
+        for _ in range(warmup):
+            step(variant)
+        torch.cuda.synchronize(dev)
+        per_y = [[] for _ in YS]
+        kern = []
+        evs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+                 torch.cuda.Event(enable_timing=True)) for _ in YS] for _ in range(steps)]
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        l0 = mego.launch_count()
+        for s in range(steps):
+            flush.zero_()
+            step(variant, evs[s])
+        torch.cuda.synchronize(dev)
+        launches = mego.launch_count() - l0
+        if dist is not None:
+            dist.barrier()
+        step_ms = []
+        for s in range(steps):
+            tot = 0.0
+            for t in range(len(YS)):
+                a, b, c = evs[s][t]
+                ms = a.elapsed_time(b)
+                per_y[t].append(ms)
+                tot += ms
+                if t == len(YS) - 1:
+                    kern.append(c.elapsed_time(b))
+            step_ms.append(tot)
+        return step_ms, per_y, kern, launches
+
+    # Launch shapes: autotune each variant on the workload (outside the timed
+    # region), the largest B last, since the device-side bound launches use
+    # the shape tuned last for their size bucket.
+    step(mego.MEGOPOLIS)
+    torch.cuda.synchronize(dev)
+    tuned = {}
+    for variant in (mego.METROPOLIS, mego.MEGOPOLIS):
+        for t in range(len(YS)):
+            B_t = int(B_dev[t].item())
+            cfg, _ = mego.mego_autotune(w_dev[t], B_t, variant, anc=anc[t], reps=2,
+                                        stream=stream)
+        tuned[variant] = cfg
+    # Verify the device bound succeeded for every y (status word) once.
+    step(mego.MEGOPOLIS)
+    Bs = []
+    for t in range(len(YS)):
+        if mego.mego_sync_status(st_dev[t], 60.0, stream) != mego.MEGO_OK:
+            raise RuntimeError("device bound failed for y=%d" % YS[t])
+        Bs.append(int(B_dev[t].item()))
+
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    time.sleep(0.3)
+    mego_ms, mego_y, mego_kern, launches = timed(mego.MEGOPOLIS, args.steps, args.warmup)
+    metro_steps = max(3, args.steps // 4)
+    metro_ms, metro_y, _, _ = timed(mego.METROPOLIS, metro_steps, args.warmup)
+    clocks = sampler.stop()
+
+    total_ms = sum(mego_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    particles = N * len(YS) * args.steps * world
+    value = particles / (total_ms / 1e3)
+    metro_value = N * len(YS) * metro_steps / (sum(metro_ms) / 1e3)
+
+    # Roofline of the dominant kernel: Megopolis at y = 4.
+    hbm_peak, peak_src = _peaks()
+    B4 = Bs[-1]
+    alg_bytes = N * (4.0 * B4 + 8.0)
+    k_ms = statistics.mean(mego_kern)
+    achieved = alg_bytes / (k_ms / 1e3) / 1e9
+    sink = torch.empty(4096, dtype=torch.float32, device=dev)
+    probe_buf = torch.empty(32 << 20, dtype=torch.uint8, device=dev)
+    mego.mego_probe_read(probe_buf, 16, sink, stream=stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l2_best = 0.0
+    for _ in range(5):
+        e0.record(stream)
+        mego.mego_probe_read(probe_buf, 128, sink, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        l2_best = max(l2_best, (32 << 20) * 128 / (e0.elapsed_time(e1) / 1e3) / 1e9)
+    del probe_buf
+
+    # Fused step (likelihood -> bound -> Megopolis + 6-dim SoA gather).
+    x = torch.from_numpy(synthetic.gaussian_state(N, 6, SEED)).to(dev)
+    x_out = torch.empty_like(x)
+    wf = torch.empty(N, dtype=torch.float32, device=dev)
+    fused = []
+    for s in range(args.warmup + max(3, args.steps // 4)):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        mego.mego_likelihood_B(x[0], 2.0, EPS, w=wf, B_dev=B_dev[0], status=st_dev[0],
+                               q=q_dev[0], ws=ws[0], stream=stream)
+        mego.mego_resample_gather(wf, 0, B_dev[0], SEED, 0, mego.MEGOPOLIS, x_in=x,
+                                  x_out=x_out, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        if s >= args.warmup:
+            fused.append(a.elapsed_time(b))
+
+    # End to end through the host-buffer C-ABI call (copies inside the region).
+    h_w = [torch.from_numpy(synthetic.gaussian_weights(N, y, SEED + y)).pin_memory() for y in YS]
+    h_anc = torch.empty(N, dtype=torch.int32).pin_memory()
+    d_sc = torch.empty(32, dtype=torch.uint8, device=dev)
+    e2e_steps = max(3, args.steps // 4)
+    for s in range(args.warmup + e2e_steps):
+        if s == args.warmup:
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+        for t in range(len(YS)):
+            mego.mego_resample_host(h_w[t], -1, EPS, SEED, 0, mego.MEGOPOLIS, h_anc, w_dev[t],
+                                    anc[t], d_sc, ws[t], stream=stream)
+    e2e_s = time.perf_counter() - t0
+    e2e_value = N * len(YS) * e2e_steps / e2e_s
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = _cpu_baseline(args.cpu_sample)
+
+    def pct(v, p):
+        v = sorted(v)
+        return v[min(len(v) - 1, int(round(p / 100.0 * (len(v) - 1))))]
+
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "scaling sweep at N=2^20: y=0..4 (x~N(0,1), "
+                               "w=exp(-(x-y)^2/2)), B from Eq. 3 at eps=0.01 on the device, "
+                               "Megopolis, int32 ancestors",
+                   "N": N, "B": dict(zip(map(str, YS), Bs)), "eps": EPS,
+                   "l2": "256 MiB buffer written between timed steps",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "launch_shape": {"megopolis": tuned[mego.MEGOPOLIS],
+                                    "metropolis": tuned[mego.METROPOLIS]}},
+        "p50_ms_per_resample": {str(y): pct(mego_y[t], 50) for t, y in enumerate(YS)},
+        "p99_ms_per_resample": {str(y): pct(mego_y[t], 99) for t, y in enumerate(YS)},
+        "metropolis": {
+            "value": metro_value, "unit": UNIT, "ms_per_step": statistics.mean(metro_ms),
+            "p50_ms_per_resample": {str(y): pct(metro_y[t], 50) for t, y in enumerate(YS)},
+            "p99_ms_per_resample": {str(y): pct(metro_y[t], 99) for t, y in enumerate(YS)},
+            "megopolis_speedup_per_y": {str(y): statistics.median(metro_y[t]) /
+                                        statistics.median(mego_y[t])
+                                        for t, y in enumerate(YS)}},
+        "fused_step": {"workload": "N=2^20, 6-dim SoA state, likelihood vs y=2, bound, "
+                                   "Megopolis, gather into a new buffer",
+                       "ms": statistics.median(fused),
+                       "value": N / (statistics.median(fused) / 1e3), "unit": UNIT},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": _profiled_traffic(),
+                     "kernel": "Megopolis resample, N=2^20, y=4, B=%d" % B4,
+                     "peak_source": peak_src,
+                     "l2_probe_gbs": l2_best, "frac_of_l2_probe": achieved / l2_best},
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": UNIT,
+                "h2d_bytes_per_step": 4 * N * len(YS),
+                "d2h_bytes_per_step": (4 * N + 8) * len(YS)},
+        "gpu_launches": launches,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-sample", type=int, default=1 << 20)
+    ap.add_argument("--reference-sample", type=int, default=1 << 12)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

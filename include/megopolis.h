@@ -80,8 +80,8 @@ typedef enum mego_path {
  * never depends on these. */
 typedef struct mego_launch_cfg {
   int32_t threads;      /* CTA size, a multiple of 32 in [64, 256]         */
-  int32_t ppt;          /* particles per thread, 1, 2 or 4 (each a 32-particle
-                           segment of one warp)                              */
+  int32_t ppt;          /* particles per thread, 1, 2, 4 or 8 (each a
+                           32-particle segment of one warp)                  */
   int32_t path;         /* mego_path                                         */
   int32_t ctas_per_sm;  /* resident CTAs per SM to aim for                   */
 } mego_launch_cfg;
@@ -183,6 +183,23 @@ mego_status mego_resample_host(const float* h_w, int32_t n, int32_t B,
  * *h_status untouched) if the stream has not drained by the deadline. */
 mego_status mego_sync_status(const int32_t* d_status, void* stream,
                              double timeout_s, int32_t* h_status);
+
+/* ----------------------------------------------------------------------
+ * Autotuner: time every launch shape (threads 64/128/256 x particles per
+ * thread 1/2/4/8 x global/shared-memory path) on the given buffers, `reps`
+ * timed runs each after one warm-up, and remember the fastest for this
+ * device, variant, gather layout, floor(log2 n) and floor(log2 B); later
+ * calls with cfg == NULL (host or device B) use it.  Arguments as in
+ * mego_resample_gather (B from the host).  Synchronises `stream`; overwrites
+ * d_anc / d_x_out.  *best and *best_ms (may be NULL) receive the winner.
+ * Shapes the library rejects (weights too large for shared memory) are
+ * skipped.  Results depend only on the inputs, never on the shape chosen.
+ */
+mego_status mego_autotune(const float* d_w, int32_t n, int32_t B, int variant,
+                          uint32_t psize_bytes, const float* d_x_in,
+                          float* d_x_out, int32_t dim, int64_t ld, int layout,
+                          int32_t* d_anc, int32_t reps, mego_launch_cfg* best,
+                          float* best_ms, void* stream);
 
 /* ----------------------------------------------------------------------
  * Measurement helper (not part of the method): read `bytes` of d_buf

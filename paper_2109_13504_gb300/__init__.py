@@ -88,6 +88,8 @@ def _load():
                                 sz, vp], ci),
         "mego_sync_status": ([vp, vp, f64, vp], ci),
         "mego_probe_read": ([vp, sz, i32, vp, vp], ci),
+        "mego_autotune": ([vp, i32, i32, ci, u32, vp, vp, i32, ctypes.c_int64, ci, vp, i32,
+                           ctypes.POINTER(LaunchCfg), ctypes.POINTER(ctypes.c_float), vp], ci),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)
@@ -282,6 +284,36 @@ def mego_sync_status(status: torch.Tensor, timeout_s: float = 10.0, stream=None)
                                   float(timeout_s), ctypes.addressof(h))
     _check(st, "mego_sync_status")
     return int(h.value)
+
+
+def mego_autotune(w: torch.Tensor, B: int, variant: int = MEGOPOLIS, psize_bytes: int = 0,
+                  x_in: Optional[torch.Tensor] = None, x_out: Optional[torch.Tensor] = None,
+                  layout: int = LAYOUT_SOA, anc: Optional[torch.Tensor] = None, reps: int = 3,
+                  stream=None):
+    """Time every launch shape and cache the fastest for this size/B bucket.
+    Returns (shape dict, milliseconds)."""
+    n = w.numel()
+    dim, ld = 0, 0
+    px_in = px_out = None
+    if x_in is not None:
+        if layout == LAYOUT_SOA:
+            dim, ld = x_in.shape[0], x_in.shape[1]
+        else:
+            dim, ld = 4, 4
+        px_in = _dev(x_in, torch.float32, "x_in")
+        px_out = _dev(x_out, torch.float32, "x_out")
+    if anc is None and x_in is None:
+        anc = torch.empty(n, dtype=torch.int32, device=w.device)
+    panc = _dev(anc, torch.int32, "anc", n) if anc is not None else None
+    best = LaunchCfg()
+    ms = ctypes.c_float()
+    st = _load().mego_autotune(_dev(w, torch.float32, "w"), n, int(B), int(variant),
+                               int(psize_bytes), px_in, px_out, int(dim), int(ld), int(layout),
+                               panc, int(reps), ctypes.byref(best), ctypes.byref(ms),
+                               _stream(stream))
+    _check(st, "mego_autotune")
+    return ({"threads": best.threads, "ppt": best.ppt, "path": best.path,
+             "ctas_per_sm": best.ctas_per_sm}, float(ms.value))
 
 
 def mego_probe_read(buf: torch.Tensor, reps: int, sink: torch.Tensor, stream=None) -> None:

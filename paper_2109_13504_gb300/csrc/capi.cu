@@ -109,16 +109,16 @@ mego_status choose_shape(int variant, uint32_t n, int gather, const mego_launch_
   int ppt = (cfg && cfg->ppt) ? cfg->ppt : 0;
   if (ppt == 0) {
     const uint64_t seg_per_sm = nseg / static_cast<uint64_t>(di.sms);
-    ppt = seg_per_sm >= 256 ? 4 : (seg_per_sm >= 64 ? 2 : 1);
+    ppt = seg_per_sm >= 128 ? 4 : (seg_per_sm >= 32 ? 2 : 1);
   }
-  if (ppt != 1 && ppt != 2 && ppt != 4) return MEGO_EINVAL;
+  if (ppt != 1 && ppt != 2 && ppt != 4 && ppt != 8) return MEGO_EINVAL;
   const size_t w_bytes = (static_cast<size_t>(n) * 4u + 15u) & ~static_cast<size_t>(15u);
   int path = (cfg && cfg->path) ? cfg->path : MEGO_PATH_AUTO;
   if (path == MEGO_PATH_AUTO)
     path = (w_bytes <= 96u * 1024u) ? MEGO_PATH_SMEM : MEGO_PATH_GLOBAL;
   if (path != MEGO_PATH_SMEM && path != MEGO_PATH_GLOBAL) return MEGO_EINVAL;
   const bool smem = path == MEGO_PATH_SMEM;
-  if (smem && w_bytes + 1024u > static_cast<size_t>(di.smem_optin)) return MEGO_EINVAL;
+  if (smem && w_bytes + 4096u > static_cast<size_t>(di.smem_optin)) return MEGO_EINVAL;
   const size_t smem_bytes = smem ? w_bytes : 0u;
   const void* kp = kernel_ptr(variant, ppt, smem, gather);
   if (!kp) return MEGO_EINVAL;
@@ -137,6 +137,64 @@ mego_status choose_shape(int variant, uint32_t n, int gather, const mego_launch_
   out->grid = static_cast<int>(grid);
   out->smem_bytes = smem_bytes;
   return MEGO_OK;
+}
+
+// Round keys of Philox4x32-10 for a seed, and the constants of the stream
+// word (c2 = stream id) used by the hoisted generator.
+mego::PhiloxKeys make_keys(uint64_t seed, uint32_t sid) {
+  mego::PhiloxKeys K;
+  uint32_t k0 = static_cast<uint32_t>(seed & 0xFFFFFFFFull);
+  uint32_t k1 = static_cast<uint32_t>(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    K.rk0[r] = k0;
+    K.rk1[r] = k1;
+    k0 += mego::kPhiloxW0;
+    k1 += mego::kPhiloxW1;
+  }
+  const uint64_t m = static_cast<uint64_t>(mego::kPhiloxM1) * sid;
+  K.H = static_cast<uint32_t>(m >> 32) ^ K.rk0[0];
+  K.L = static_cast<uint32_t>(m);
+  K.sid = sid;
+  return K;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuning cache: best launch shape per (device, variant, gather layout,
+// floor(log2 n), bucket of B).  Filled by mego_autotune, read when the caller
+// passes no shape.
+
+using TuneKey = std::tuple<int, int, int, int, int>;
+
+int b_bucket(int32_t B) {
+  int b = 0;
+  while (b < 30 && (1 << (b + 1)) <= B) ++b;
+  return B <= 0 ? -1 : b;
+}
+
+int n_bucket(uint32_t n) {
+  int b = 0;
+  while (b < 31 && (1u << (b + 1)) <= n) ++b;
+  return b;
+}
+
+std::mutex g_tune_mu;
+std::map<TuneKey, mego_launch_cfg> g_tune;
+
+bool tune_lookup(int variant, int gather, uint32_t n, int32_t B, mego_launch_cfg* out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tune.find(TuneKey(dev, variant, gather, n_bucket(n), b_bucket(B)));
+  if (it == g_tune.end()) return false;
+  *out = it->second;
+  return true;
+}
+
+void tune_store(int variant, int gather, uint32_t n, int32_t B, const mego_launch_cfg& c) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune[TuneKey(dev, variant, gather, n_bucket(n), b_bucket(B))] = c;
 }
 
 mego_status check_partition(int variant, uint32_t n, uint32_t psize, uint32_t* nw,
@@ -240,6 +298,8 @@ mego_status mego_resample_gather(const float* d_w, int32_t n, int32_t B, const i
   if (d_anc && d_x_out && overlaps(d_anc, w_bytes, d_x_out, x_bytes)) return MEGO_EINVAL;
   if (d_x_out && overlaps(d_x_out, x_bytes, d_w, w_bytes)) return MEGO_EINVAL;
 
+  mego_launch_cfg tuned;
+  if (!cfg && tune_lookup(variant, gather, un, d_B ? -1 : B, &tuned)) cfg = &tuned;
   mego::LaunchShape shape;
   mego_status st = choose_shape(variant, un, gather, cfg, &shape);
   if (st != MEGO_OK) return st;
@@ -256,9 +316,7 @@ mego_status mego_resample_gather(const float* d_w, int32_t n, int32_t B, const i
   a.n = un;
   a.nseg = (un + 31u) / 32u;
   a.B = d_B ? 0 : B;
-  a.k0 = static_cast<uint32_t>(seed & 0xFFFFFFFFull);
-  a.k1 = static_cast<uint32_t>(seed >> 32);
-  a.sid = stream_id;
+  a.K = make_keys(seed, stream_id);
   a.dim = dim;
   a.nw = nw;
   a.npart = npart;
@@ -385,6 +443,77 @@ mego_status mego_resample_host(const float* h_w, int32_t n, int32_t B, double ep
   if (cudaStreamSynchronize(st) != cudaSuccess) return MEGO_ECUDA;
   if (h_B) *h_B = hb[0];
   return hb[1] == 0 ? MEGO_OK : MEGO_EWEIGHTS;
+}
+
+mego_status mego_autotune(const float* d_w, int32_t n, int32_t B, int variant,
+                          uint32_t psize_bytes, const float* d_x_in, float* d_x_out,
+                          int32_t dim, int64_t ld, int layout, int32_t* d_anc, int32_t reps,
+                          mego_launch_cfg* best, float* best_ms, void* stream) {
+  if (B < 0 || B > MEGO_B_MAX || reps < 1 || reps > 100) return MEGO_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return MEGO_ECUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return MEGO_ECUDA;
+  }
+  const int threads_c[] = {64, 128, 256};
+  const int ppt_c[] = {1, 2, 4, 8};
+  const int path_c[] = {MEGO_PATH_GLOBAL, MEGO_PATH_SMEM};
+  mego_launch_cfg win{0, 0, 0, 0};
+  float win_ms = 1e30f;
+  mego_status status = MEGO_OK;
+  for (int path : path_c) {
+    for (int threads : threads_c) {
+      for (int ppt : ppt_c) {
+        mego_launch_cfg c{threads, ppt, path, 0};
+        // Warm-up launch; shapes the library rejects (e.g. weights that do
+        // not fit shared memory) are skipped.
+        mego_status s = mego_resample_gather(d_w, n, B, nullptr, 1u, 0u, variant, psize_bytes,
+                                             d_x_in, d_x_out, dim, ld, layout, d_anc, &c,
+                                             stream);
+        if (s == MEGO_EINVAL) continue;
+        if (s != MEGO_OK) {
+          status = s;
+          break;
+        }
+        float total = 0.0f;
+        bool ok = true;
+        for (int r = 0; r < reps && ok; ++r) {
+          ok = cudaEventRecord(e0, st) == cudaSuccess;
+          ok = ok && mego_resample_gather(d_w, n, B, nullptr, 1u, 0u, variant, psize_bytes,
+                                          d_x_in, d_x_out, dim, ld, layout, d_anc, &c,
+                                          stream) == MEGO_OK;
+          ok = ok && cudaEventRecord(e1, st) == cudaSuccess;
+          ok = ok && cudaEventSynchronize(e1) == cudaSuccess;
+          float ms = 0.0f;
+          ok = ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+          total += ms;
+        }
+        if (!ok) {
+          status = MEGO_ECUDA;
+          break;
+        }
+        if (total / reps < win_ms) {
+          win_ms = total / reps;
+          win = c;
+        }
+      }
+      if (status != MEGO_OK) break;
+    }
+    if (status != MEGO_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (status != MEGO_OK) return status;
+  if (win.threads == 0) return MEGO_EINVAL;
+  int gather = mego::kGatherNone;
+  if (d_x_in) gather = layout == MEGO_LAYOUT_AOS4 ? mego::kGatherAos4 : mego::kGatherSoa;
+  tune_store(variant, gather, static_cast<uint32_t>(n), B, win);
+  tune_store(variant, gather, static_cast<uint32_t>(n), -1, win);  // device-side B
+  if (best) *best = win;
+  if (best_ms) *best_ms = win_ms;
+  return MEGO_OK;
 }
 
 mego_status mego_probe_read(const void* d_buf, size_t bytes, int32_t reps, float* d_sink,

@@ -14,28 +14,91 @@ constexpr uint32_t kTagMetro = 3u;   // Metropolis (j, u) pairs
 constexpr uint32_t kTagCPart = 4u;   // C1/C2 per-warp partition
 constexpr uint32_t kTagCDraw = 5u;   // C1/C2 (j in partition, u) pairs
 
-// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of
-//   (c0,c1,c2,c3) <- (hi(M1 c2) ^ c1 ^ k0, M1 c2, hi(M0 c0) ^ c3 ^ k1, M0 c0)
-// with the key advanced by the Weyl increments between rounds.  Loop
-// invariant parts (a fixed c0 or c2) are hoisted by the compiler.
-__device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1,
-                                               uint32_t c2, uint32_t c3,
-                                               uint32_t k0, uint32_t k1) {
-  constexpr uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
-  constexpr uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u, kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u, kPhiloxW1 = 0xBB67AE85u;
+
+// Round keys and stream constants of one launch, computed on the host:
+// rk0[r] = k0 + r W0, rk1[r] = k1 + r W1 (the key of round r), and for the
+// stream word c2 = sid: H = hi(M1 sid) ^ rk0[0], L = lo(M1 sid).  Passed in
+// the kernel parameters, so every round reads its key from the constant bank.
+struct PhiloxKeys {
+  uint32_t rk0[10];
+  uint32_t rk1[10];
+  uint32_t H, L;
+  uint32_t sid;
+};
+
+__device__ __forceinline__ uint64_t mulwide(uint32_t a, uint32_t b) {
+  return static_cast<uint64_t>(a) * static_cast<uint64_t>(b);
+}
+__device__ __forceinline__ uint32_t hi32(uint64_t x) { return static_cast<uint32_t>(x >> 32); }
+__device__ __forceinline__ uint32_t lo32(uint64_t x) { return static_cast<uint32_t>(x); }
+
+// One Philox4x32 round with key (k0, k1):
+//   (c0,c1,c2,c3) <- (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0))
+__device__ __forceinline__ void philox_round(uint32_t& c0, uint32_t& c1, uint32_t& c2,
+                                             uint32_t& c3, uint32_t k0, uint32_t k1) {
+  const uint64_t p0 = mulwide(kPhiloxM0, c0);
+  const uint64_t p1 = mulwide(kPhiloxM1, c2);
+  c0 = hi32(p1) ^ c1 ^ k0;
+  c1 = lo32(p1);
+  c2 = hi32(p0) ^ c3 ^ k1;
+  c3 = lo32(p0);
+}
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds, round r
+// keyed by (k0 + r W0, k1 + r W1).
+__device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2,
+                                               uint32_t c3, const PhiloxKeys& K) {
 #pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    const uint32_t h0 = __umulhi(M0, c0), l0 = M0 * c0;
-    const uint32_t h1 = __umulhi(M1, c2), l1 = M1 * c2;
-    c0 = h1 ^ c1 ^ k0;
-    c1 = l1;
-    c2 = h0 ^ c3 ^ k1;
-    c3 = l0;
-    k0 += W0;
-    k1 += W1;
-  }
+  for (int r = 0; r < 10; ++r) philox_round(c0, c1, c2, c3, K.rk0[r], K.rk1[r]);
   return make_uint4(c0, c1, c2, c3);
 }
+
+// Philox4x32-10 for the counter family (i, g, sid, tag) with the particle i
+// and the tag fixed and g varying.  Everything that depends only on (i, tag)
+// -- round 0, the c0/c1 half of round 1 and the c0 product of round 2 -- is
+// computed once by init(); the part that depends only on g (the c0 product of
+// round 1) is shared by all particles of a thread (group()).  gen() finishes
+// the ten rounds.  The output equals philox4x32_10(i, g, sid, tag).
+struct PhiloxLane {
+  uint32_t x1;    // c3 after round 0, xored with the round-1 key word rk1[1]
+  uint32_t c1_2;  // c1 after round 1
+  uint32_t h3;    // hi(M0 * c0) in round 2
+  uint32_t l3;    // lo(M0 * c0) in round 2 (= c3 after round 2)
+
+  __device__ __forceinline__ void init(uint32_t i, uint32_t tag, const PhiloxKeys& K) {
+    const uint64_t p0 = mulwide(kPhiloxM0, i);
+    const uint32_t c2_1 = hi32(p0) ^ tag ^ K.rk1[0];
+    x1 = lo32(p0) ^ K.rk1[1];
+    const uint64_t p1 = mulwide(kPhiloxM1, c2_1);
+    const uint32_t c0_2 = hi32(p1) ^ K.L ^ K.rk0[1];
+    c1_2 = lo32(p1);
+    const uint64_t p2 = mulwide(kPhiloxM0, c0_2);
+    h3 = hi32(p2);
+    l3 = lo32(p2);
+  }
+
+  // Shared per g: round-1 c0 product of c0_1 = H ^ g.
+  static __device__ __forceinline__ void group(uint32_t g, const PhiloxKeys& K,
+                                               uint32_t& mh, uint32_t& ml) {
+    const uint64_t m = mulwide(kPhiloxM0, K.H ^ g);
+    mh = hi32(m);
+    ml = lo32(m);
+  }
+
+  __device__ __forceinline__ uint4 gen(uint32_t mh, uint32_t ml, const PhiloxKeys& K) const {
+    // after round 1: (c0_2, c1_2, mh ^ x1, ml); round 2 needs c2_2 = mh ^ x1.
+    const uint64_t p = mulwide(kPhiloxM1, mh ^ x1);
+    uint32_t c0 = hi32(p) ^ c1_2 ^ K.rk0[2];
+    uint32_t c1 = lo32(p);
+    uint32_t c2 = h3 ^ ml ^ K.rk1[2];
+    uint32_t c3 = l3;
+#pragma unroll
+    for (int r = 3; r < 10; ++r) philox_round(c0, c1, c2, c3, K.rk0[r], K.rk1[r]);
+    return make_uint4(c0, c1, c2, c3);
+  }
+};
 
 // u in (0,1] from the low 23 bits of a word: 2 - 1.m, exact.
 __device__ __forceinline__ float u_of(uint32_t word) {
@@ -58,11 +121,10 @@ __device__ __forceinline__ uint32_t index32(uint32_t x, uint32_t n) {
   return __umulhi(x, n);
 }
 
-// Megopolis offset o^(b) ~ U{0, n-1}.
-__device__ __forceinline__ uint32_t mego_offset(uint32_t k0, uint32_t k1,
-                                                uint32_t sid, uint32_t b,
+// Megopolis offset o^(b) ~ U{0, n-1}: Philox counter (b, 0, sid, 1).
+__device__ __forceinline__ uint32_t mego_offset(const PhiloxKeys& K, uint32_t b,
                                                 uint32_t n) {
-  const uint4 x = philox4x32_10(b, 0u, sid, kTagOffset, k0, k1);
+  const uint4 x = philox4x32_10(b, 0u, K.sid, kTagOffset, K);
   return index64(x.x, x.y, n);
 }
 

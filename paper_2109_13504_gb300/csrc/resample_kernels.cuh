@@ -32,11 +32,15 @@ struct ResampleArgs {
   uint32_t n;
   uint32_t nseg;         // ceil(n / 32)
   int32_t B;
-  uint32_t k0, k1, sid;
   int32_t dim;
   uint32_t nw;           // C1/C2: weights per partition
   uint32_t npart;        // C1/C2: number of partitions
+  PhiloxKeys K;          // round keys for (seed, stream id)
 };
+
+// Per-warp table of the 32 iterations of the current offset window:
+// (wrapped partition base of the warp's first segment, offset o^(b)).
+constexpr int kMaxWarps = 8;
 
 extern __shared__ float4 g_dyn_smem[];
 
@@ -117,81 +121,126 @@ __device__ __forceinline__ void finish_batch(const ResampleArgs& a, uint32_t iba
   }
 }
 
+// Loads of one Megopolis iteration for the P segments of a batch when the
+// partitions may run past n: each index is reduced modulo n.
+template <int P, bool SMEM>
+__device__ __forceinline__ void mego_wrapped_loads(const ResampleArgs& a, int2 e,
+                                                   uint32_t lane, float (&wj)[P]) {
+  const uint32_t n = a.n;
+  const uint32_t x0 = static_cast<uint32_t>(e.x) + ((lane + static_cast<uint32_t>(e.y)) & 31u);
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    uint32_t j = x0 + 32u * p;
+    if (j >= n) j -= n;
+    if (j >= n) j %= n;
+    wj[p] = ldw<SMEM>(a.w, j);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Megopolis (Algorithm 5).  Iteration b, particle i = 32 s + lane:
 //   j = (32 s + o_al + (lane + o) mod 32) mod n,  o_al = o - o mod 32.
 // The warp reads one aligned 32-weight partition per segment and iteration.
-// Chains keep k - 32 p ("relative" ancestor) so that in the common case, where
-// the P partitions do not wrap past n, every particle's candidate is the one
-// shared window index x0.
+// Every 32 iterations each lane draws the offset of one iteration and stores
+// (wrapped base of the warp's first segment, offset) in the warp's table;
+// a ballot marks the iterations whose P partitions do not run past n, so the
+// common case loads at x0 + 32 p with immediate offsets.  Chains record the
+// iteration b of their last acceptance (a uniform value) and the ancestor
+// index is rebuilt from o^(b) once, after the last iteration.
 template <int P, bool SMEM, int GATHER>
 __device__ __forceinline__ void megopolis_batch(const ResampleArgs& a, int B,
                                                 uint32_t s0, uint32_t seg_hi,
-                                                uint32_t lane) {
+                                                uint32_t lane, int2* win) {
   const uint32_t n = a.n;
   const uint32_t ibase = s0 * 32u + lane;
   float wk[P];
-  uint32_t kr[P];
+  int kb[P];
   bool live[P];
+  PhiloxLane ph[P];
 #pragma unroll
   for (int p = 0; p < P; ++p) {
     const uint32_t i = ibase + 32u * p;
     live[p] = (s0 + p < seg_hi) && (i < n);
     wk[p] = ldw<SMEM>(a.w, i < n ? i : n - 1u);
-    kr[p] = ibase;
+    kb[p] = -1;
+    ph[p].init(i, kTagMegoU, a.K);
   }
-  uint32_t o_reg = 0u;
+  uint32_t fast_mask = 0u;
   for (int b0 = 0; b0 < B; b0 += 4) {
-    if ((b0 & 31) == 0)
-      o_reg = mego_offset(a.k0, a.k1, a.sid, static_cast<uint32_t>(b0) + lane, n);
-    const int nb = (B - b0) < 4 ? (B - b0) : 4;
-    float wj[4][P];
-    uint32_t cj[4][P];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      if (q < nb) {
-        const uint32_t o = __shfl_sync(0xFFFFFFFFu, o_reg, (b0 + q) & 31);
-        uint32_t base = s0 * 32u + (o & ~31u);
-        base = base >= n ? base - n : base;
-        const uint32_t x0 = base + ((lane + o) & 31u);
-        if (base + 32u * P <= n) {
-#pragma unroll
-          for (int p = 0; p < P; ++p) {
-            wj[q][p] = ldw<SMEM>(a.w, x0 + 32u * p);
-            cj[q][p] = x0;
-          }
-        } else {
-#pragma unroll
-          for (int p = 0; p < P; ++p) {
-            uint32_t j = x0 + 32u * p;
-            if (j >= n) j -= n;
-            if (j >= n) j %= n;
-            wj[q][p] = ldw<SMEM>(a.w, j);
-            cj[q][p] = j - 32u * p;
-          }
-        }
-      }
+    if ((b0 & 31) == 0) {
+      const uint32_t o = mego_offset(a.K, static_cast<uint32_t>(b0) + lane, n);
+      uint32_t base = s0 * 32u + (o & ~31u);
+      base = base >= n ? base - n : base;
+      fast_mask = __ballot_sync(0xFFFFFFFFu, base + 32u * P <= n);
+      __syncwarp();
+      win[lane] = make_int2(static_cast<int>(base), static_cast<int>(o));
+      __syncwarp();
     }
-    uint4 r[P];
+    const int t0 = b0 & 31;
+    uint32_t mh, ml;
+    PhiloxLane::group(static_cast<uint32_t>(b0) >> 2, a.K, mh, ml);
+    float wj[4][P];
+    if (B - b0 >= 4) {
+      // Four full iterations.
+      if (((fast_mask >> t0) & 0xFu) == 0xFu) {
 #pragma unroll
-    for (int p = 0; p < P; ++p)
-      r[p] = philox4x32_10(ibase + 32u * p, static_cast<uint32_t>(b0) >> 2, a.sid,
-                           kTagMegoU, a.k0, a.k1);
+        for (int q = 0; q < 4; ++q) {
+          const int2 e = win[t0 + q];
+          const uint32_t x0 = static_cast<uint32_t>(e.x) +
+                              ((lane + static_cast<uint32_t>(e.y)) & 31u);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      if (q < nb) {
+          for (int p = 0; p < P; ++p) wj[q][p] = ldw<SMEM>(a.w, x0 + 32u * p);
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) mego_wrapped_loads<P, SMEM>(a, win[t0 + q], lane, wj[q]);
+      }
+      uint4 r[P];
+#pragma unroll
+      for (int p = 0; p < P; ++p) r[p] = ph[p].gen(mh, ml, a.K);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
 #pragma unroll
         for (int p = 0; p < P; ++p) {
           const bool acc = accept(u_of(word_of(r[p], q)), wk[p], wj[q][p]);
           wk[p] = acc ? wj[q][p] : wk[p];
-          kr[p] = acc ? cj[q][p] : kr[p];
+          kb[p] = acc ? b0 + q : kb[p];
+        }
+      }
+    } else {
+      // Tail: 1..3 iterations.
+      const int nb = B - b0;
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+        if (q < nb) mego_wrapped_loads<P, SMEM>(a, win[t0 + q], lane, wj[q]);
+      uint4 r[P];
+#pragma unroll
+      for (int p = 0; p < P; ++p) r[p] = ph[p].gen(mh, ml, a.K);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        if (q < nb) {
+#pragma unroll
+          for (int p = 0; p < P; ++p) {
+            const bool acc = accept(u_of(word_of(r[p], q)), wk[p], wj[q][p]);
+            wk[p] = acc ? wj[q][p] : wk[p];
+            kb[p] = acc ? b0 + q : kb[p];
+          }
         }
       }
     }
   }
   uint32_t k[P];
 #pragma unroll
-  for (int p = 0; p < P; ++p) k[p] = kr[p] + 32u * p;
+  for (int p = 0; p < P; ++p) {
+    k[p] = ibase + 32u * p;
+    if (kb[p] >= 0) {
+      const uint32_t o = mego_offset(a.K, static_cast<uint32_t>(kb[p]), n);
+      uint32_t x = (s0 + p) * 32u + (o & ~31u) + ((lane + o) & 31u);
+      if (x >= n) x -= n;
+      if (x >= n) x %= n;
+      k[p] = x;
+    }
+  }
   finish_batch<P, GATHER>(a, ibase, k, live);
 }
 
@@ -207,20 +256,22 @@ __device__ __forceinline__ void metropolis_batch(const ResampleArgs& a, int B,
   float wk[P];
   uint32_t k[P];
   bool live[P];
+  PhiloxLane ph[P];
 #pragma unroll
   for (int p = 0; p < P; ++p) {
     const uint32_t i = ibase + 32u * p;
     live[p] = (s0 + p < seg_hi) && (i < n);
     k[p] = i < n ? i : n - 1u;
     wk[p] = ldw<SMEM>(a.w, k[p]);
+    ph[p].init(i, kTagMetro, a.K);
   }
   for (int b0 = 0; b0 < B; b0 += 2) {
     const int nb = (B - b0) < 2 ? (B - b0) : 2;
+    uint32_t mh, ml;
+    PhiloxLane::group(static_cast<uint32_t>(b0) >> 1, a.K, mh, ml);
     uint4 r[P];
 #pragma unroll
-    for (int p = 0; p < P; ++p)
-      r[p] = philox4x32_10(ibase + 32u * p, static_cast<uint32_t>(b0) >> 1, a.sid,
-                           kTagMetro, a.k0, a.k1);
+    for (int p = 0; p < P; ++p) r[p] = ph[p].gen(mh, ml, a.K);
     float wj[2][P];
     uint32_t jj[2][P];
 #pragma unroll
@@ -261,15 +312,17 @@ __device__ __forceinline__ void partition_batch(const ResampleArgs& a, int B,
   uint32_t k[P];
   bool live[P];
   uint32_t part[P];
+  PhiloxLane ph[P];
 #pragma unroll
   for (int p = 0; p < P; ++p) {
     const uint32_t i = ibase + 32u * p;
     live[p] = (s0 + p < seg_hi) && (i < n);
     k[p] = i < n ? i : n - 1u;
     wk[p] = ldw<SMEM>(a.w, k[p]);
+    ph[p].init(i, kTagCDraw, a.K);
     part[p] = 0u;
     if constexpr (VARIANT == kC1) {
-      const uint4 x = philox4x32_10(s0 + p, 0u, a.sid, kTagCPart, a.k0, a.k1);
+      const uint4 x = philox4x32_10(s0 + p, 0u, a.K.sid, kTagCPart, a.K);
       part[p] = index64(x.x, x.y, a.npart);
     }
   }
@@ -282,15 +335,15 @@ __device__ __forceinline__ void partition_batch(const ResampleArgs& a, int B,
     if constexpr (VARIANT == kC2) {
       if ((b0 % kStepsPerFill) == 0) {
         const uint32_t bb = static_cast<uint32_t>(b0) + lane / P;
-        const uint4 x = philox4x32_10(s0 + lane % P, bb + 1u, a.sid, kTagCPart, a.k0, a.k1);
+        const uint4 x = philox4x32_10(s0 + lane % P, bb + 1u, a.K.sid, kTagCPart, a.K);
         part_reg = index64(x.x, x.y, a.npart);
       }
     }
+    uint32_t mh, ml;
+    PhiloxLane::group(static_cast<uint32_t>(b0) >> 1, a.K, mh, ml);
     uint4 r[P];
 #pragma unroll
-    for (int p = 0; p < P; ++p)
-      r[p] = philox4x32_10(ibase + 32u * p, static_cast<uint32_t>(b0) >> 1, a.sid,
-                           kTagCDraw, a.k0, a.k1);
+    for (int p = 0; p < P; ++p) r[p] = ph[p].gen(mh, ml, a.K);
     float wj[2][P];
     uint32_t jj[2][P];
 #pragma unroll
@@ -325,7 +378,8 @@ __device__ __forceinline__ void partition_batch(const ResampleArgs& a, int B,
 
 // ---------------------------------------------------------------------------
 template <int VARIANT, int P, bool SMEM, int GATHER>
-__global__ void __launch_bounds__(256) resample_kernel(const ResampleArgs a) {
+__global__ void __launch_bounds__(256) resample_kernel(const __grid_constant__ ResampleArgs a) {
+  __shared__ int2 s_win[kMaxWarps][32];
   const int B = a.B_dev ? *a.B_dev : a.B;
   if (B < 0) return;  // device-side bound failed: write nothing
   if constexpr (SMEM) {
@@ -335,11 +389,14 @@ __global__ void __launch_bounds__(256) resample_kernel(const ResampleArgs a) {
   const uint32_t wpb = blockDim.x >> 5;
   const uint64_t gw = static_cast<uint64_t>(blockIdx.x) * wpb + (threadIdx.x >> 5);
   const uint64_t tw = static_cast<uint64_t>(gridDim.x) * wpb;
-  const uint32_t seg_lo = static_cast<uint32_t>(a.nseg * gw / tw);
-  const uint32_t seg_hi = static_cast<uint32_t>(a.nseg * (gw + 1u) / tw);
+  // Whole batches of P segments per warp, in equal contiguous ranges.
+  const uint64_t nbat = (a.nseg + P - 1u) / P;
+  const uint32_t seg_lo = static_cast<uint32_t>(nbat * gw / tw) * P;
+  uint32_t seg_hi = static_cast<uint32_t>(nbat * (gw + 1u) / tw) * P;
+  if (seg_hi > a.nseg) seg_hi = a.nseg;
   for (uint32_t s0 = seg_lo; s0 < seg_hi; s0 += P) {
     if constexpr (VARIANT == kMegopolis) {
-      megopolis_batch<P, SMEM, GATHER>(a, B, s0, seg_hi, lane);
+      megopolis_batch<P, SMEM, GATHER>(a, B, s0, seg_hi, lane, s_win[threadIdx.x >> 5]);
     } else if constexpr (VARIANT == kMetropolis) {
       metropolis_batch<P, SMEM, GATHER>(a, B, s0, seg_hi, lane);
     } else {

@@ -58,7 +58,7 @@ def test_small_config_bit_exact(variant):
 
 @pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("path", [mego.PATH_GLOBAL, mego.PATH_SMEM])
-@pytest.mark.parametrize("ppt", [1, 2, 4])
+@pytest.mark.parametrize("ppt", [1, 2, 4, 8])
 @pytest.mark.parametrize("threads", [64, 256])
 def test_launch_shape_invariance(variant, path, ppt, threads):
     n = 4096 + 1000 + 3
@@ -314,10 +314,24 @@ def test_host_buffer_call_matches_device_call():
 
 @pytest.mark.parametrize("variant", [mego.METROPOLIS_C1, mego.METROPOLIS_C2])
 @pytest.mark.parametrize("psize", [128, 512, 2048])
-@pytest.mark.parametrize("ppt", [1, 2, 4])
+@pytest.mark.parametrize("ppt", [1, 2, 4, 8])
 def test_partition_variants_bit_exact(variant, psize, ppt):
     n = 1 << 13
     w_h = synthetic.gaussian_weights(n, 2.0, 7)
     ref = oracle.resample(w_h, 37, 8, variant, psize_bytes=psize)
     got = _anc(w_h, 37, 8, variant, cfg={"ppt": ppt}, psize=psize)
     assert np.array_equal(got, ref)
+
+
+def test_autotune_picks_a_shape_and_keeps_results_exact():
+    n = 50_000
+    w_h = synthetic.gaussian_weights(n, 3.0, 13)
+    w = _gpu(w_h)
+    cfg, ms = mego.mego_autotune(w, 60, mego.MEGOPOLIS)
+    assert cfg["threads"] in (64, 128, 256) and cfg["ppt"] in (1, 2, 4, 8)
+    assert cfg["path"] in (mego.PATH_GLOBAL, mego.PATH_SMEM) and ms > 0
+    got = _anc(w_h, 60, 5, mego.MEGOPOLIS)            # no cfg: the tuned shape
+    assert np.array_equal(got, oracle.resample(w_h, 60, 5, mego.MEGOPOLIS))
+    for ppt in (1, 2, 4, 8):
+        got = _anc(w_h, 60, 5, mego.MEGOPOLIS, cfg={"ppt": ppt, "threads": 128})
+        assert np.array_equal(got, oracle.resample(w_h, 60, 5, mego.MEGOPOLIS))
