@@ -148,6 +148,28 @@ mego_status mego_compute_B(const float* d_w, int32_t n, double eps,
                            void* stream);
 
 /* ----------------------------------------------------------------------
+ * The iteration bound with no workspace argument and no allocation, for
+ * callers that cannot allocate device memory: for example a host
+ * application that hands out every byte of device memory from its own pool,
+ * or a real-time loop that must not call the allocator once it is running
+ * (cudaMalloc may synchronise the device and takes unbounded time).  The
+ * paper has no counterpart; this is a library convenience.
+ * Same inputs, outputs and device-side status as mego_compute_B.  The
+ * reduction's partial results go to a fixed 8 KiB array inside the library
+ * (512 partials; every GPU that loads the library keeps it until exit).
+ * The first call on a device looks up that array's device address, so make
+ * that first call before any stream capture.  All calls share the array:
+ * calls whose work overlaps on the GPU (other streams, other threads) race
+ * and may return a wrong B; order them on one stream.  Nothing in the array
+ * needs to start at zero.  n above MEGO_N_MAX is rejected with MEGO_EINVAL;
+ * any n up to it fits, since the reduction never uses more than 512 CTAs.
+ */
+mego_status mego_compute_B_noalloc(const float* d_w, int32_t n, double eps,
+                                   int32_t b_max, int32_t* d_B,
+                                   int32_t* d_status, double* d_q,
+                                   void* stream);
+
+/* ----------------------------------------------------------------------
  * Likelihood weights fused with the bound: w_i = exp(-(x_i - y)^2 / 2)
  * from row 0 of an SoA state (Eq. 12 without its constant factor, the
  * update of Algorithm 1), then B as in mego_compute_B.

@@ -3,7 +3,8 @@ GB300).  Argument marshalling only: every step runs in the library's CUDA
 kernels.  torch supplies device memory and the current CUDA stream.
 
 The functions carry the C ABI's names (``mego_resample``,
-``mego_resample_gather``, ``mego_compute_B``, ``mego_likelihood_B``,
+``mego_resample_gather``, ``mego_compute_B``, ``mego_compute_B_noalloc``,
+``mego_likelihood_B``,
 ``mego_resample_host``, ``mego_sync_status``, ``mego_probe_read``); they take
 torch tensors instead of raw pointers and raise ``MegoError`` on a non-OK
 status.  ``resample`` is a convenience wrapper that allocates the output.
@@ -82,6 +83,7 @@ def _load():
                                   ctypes.c_int64, ci, vp, ctypes.POINTER(LaunchCfg), vp],
                                  ci),
         "mego_compute_B": ([vp, i32, f64, i32, vp, vp, vp, vp, sz, vp], ci),
+        "mego_compute_B_noalloc": ([vp, i32, f64, i32, vp, vp, vp, vp], ci),
         "mego_likelihood_B": ([vp, i32, ctypes.c_float, f64, i32, vp, vp, vp, vp, vp,
                                sz, vp], ci),
         "mego_resample_host": ([vp, i32, i32, f64, u64, u32, ci, vp, vp, vp, vp, vp, vp,
@@ -234,6 +236,24 @@ def mego_compute_B(w: torch.Tensor, eps: float = 0.01, b_max: int = B_MAX,
                                 _dev(q, torch.float64, "q", 1),
                                 _dev(ws, torch.uint8, "ws"), ws.numel(), _stream(stream))
     _check(st, "mego_compute_B")
+    return B_dev, status, q
+
+
+def mego_compute_B_noalloc(w: torch.Tensor, eps: float, B_dev: torch.Tensor,
+                           status: torch.Tensor, q: Optional[torch.Tensor] = None,
+                           b_max: int = B_MAX, stream=None):
+    """Eq. 3 on the device without a workspace: for callers that cannot
+    allocate device memory.  The output tensors are the caller's (nothing is
+    allocated here); the library keeps the reduction's partials in a fixed
+    array of its own.  Calls that overlap on the GPU share that array and
+    race, so issue them on one stream.  Returns (B_dev, status, q)."""
+    n = w.numel()
+    pq = _dev(q, torch.float64, "q", 1) if q is not None else None
+    st = _load().mego_compute_B_noalloc(_dev(w, torch.float32, "w"), n, float(eps),
+                                        int(b_max), _dev(B_dev, torch.int32, "B_dev", 1),
+                                        _dev(status, torch.int32, "status", 1), pq,
+                                        _stream(stream))
+    _check(st, "mego_compute_B_noalloc")
     return B_dev, status, q
 
 
