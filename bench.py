@@ -136,6 +136,20 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def replica_aggregate(local_ms: float, local_particles: int, dist=None, device=None):
+    """Whole-job figures of N independent replicas: the slowest rank's time
+    and the particles of all ranks (value = particles / slowest time)."""
+    if dist is None:
+        return local_ms, local_particles
+    import torch
+    t = torch.tensor([local_ms, float(local_particles)], dtype=torch.float64, device=device)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = t.clone()
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0].item()), int(sm[1].item())
+
+
 def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -257,9 +271,12 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize(dev)
         l0 = mego.launch_count()
+        torch.cuda.nvtx.range_push("timed_%s" % ("megopolis" if variant == mego.MEGOPOLIS
+                                                 else "metropolis"))
         for s in range(steps):
             flush.zero_()
             step(variant, evs[s])
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize(dev)
         launches = mego.launch_count() - l0
         if dist is not None:
@@ -305,21 +322,24 @@ def run_gpu(args):
     metro_ms, metro_y, _, _ = timed(mego.METROPOLIS, metro_steps, args.warmup)
     clocks = sampler.stop()
 
-    total_ms = sum(mego_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    particles = N * len(YS) * args.steps * world
+    total_ms, particles = replica_aggregate(sum(mego_ms), N * len(YS) * args.steps, dist, dev)
     value = particles / (total_ms / 1e3)
     metro_value = N * len(YS) * metro_steps / (sum(metro_ms) / 1e3)
 
-    # Roofline of the dominant kernel: Megopolis at y = 4.
+    # Roofline of the dominant kernel: Megopolis at y = 4.  It is bound by
+    # the integer-multiply (FMA-heavy) and ALU pipes that Philox4x32-10 needs,
+    # not by memory: peak proposal rate = SMs x 32 wide 32x32-bit multiplies
+    # per SM-cycle x SM clock / 3.75 multiplies per proposal (15 of the 20
+    # multiplies of a 4-word Philox call vary with the iteration).
     hbm_peak, peak_src = _peaks()
     B4 = Bs[-1]
-    alg_bytes = N * (4.0 * B4 + 8.0)
     k_ms = statistics.mean(mego_kern)
-    achieved = alg_bytes / (k_ms / 1e3) / 1e9
+    alg_bytes = N * (4.0 * B4 + 8.0)
+    achieved_gbs = alg_bytes / (k_ms / 1e3) / 1e9
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk_mhz = clocks.get("sm_max_mhz") or 2070.0
+    peak_gprop = sms * 32.0 * clk_mhz * 1e6 / 3.75 / 1e9
+    achieved_gprop = N * B4 / (k_ms / 1e3) / 1e9
     sink = torch.empty(4096, dtype=torch.float32, device=dev)
     probe_buf = torch.empty(32 << 20, dtype=torch.uint8, device=dev)
     mego.mego_probe_read(probe_buf, 16, sink, stream=stream)
@@ -413,11 +433,20 @@ def run_gpu(args):
                                    "Megopolis, gather into a new buffer",
                        "ms": statistics.median(fused),
                        "value": N / (statistics.median(fused) / 1e3), "unit": UNIT},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "traffic": _profiled_traffic(),
-                     "kernel": "Megopolis resample, N=2^20, y=4, B=%d" % B4,
-                     "peak_source": peak_src,
-                     "l2_probe_gbs": l2_best, "frac_of_l2_probe": achieved / l2_best},
+        "roofline": {"bound": "alu", "achieved": achieved_gprop, "peak": peak_gprop,
+                     "unit": "Gproposals/s", "frac": achieved_gprop / peak_gprop,
+                     "traffic": _profiled_traffic(),
+                     "kernel": "Megopolis resample, N=2^20, y=4, B=%d, %.1f us/launch"
+                               % (B4, 1e3 * k_ms),
+                     "peak_derivation": "%d SMs x 32 32x32->64-bit multiplies per SM-cycle "
+                                        "(FMA-heavy pipe) x %.0f MHz / 3.75 multiplies per "
+                                        "proposal" % (sms, clk_mhz),
+                     "memory_view": {"algorithmic_bytes_per_launch": alg_bytes,
+                                     "achieved_gbs": achieved_gbs,
+                                     "hbm_peak_gbs": hbm_peak, "hbm_peak_source": peak_src,
+                                     "frac_of_hbm": achieved_gbs / hbm_peak,
+                                     "l2_probe_gbs": l2_best,
+                                     "frac_of_l2_probe": achieved_gbs / l2_best}},
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": 4 * N * len(YS),
@@ -430,6 +459,48 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+PROFILE_CASES = {
+    # name: (variant, log2 N, y, path, gather)
+    "mego_global_n2p20_y4": ("megopolis", 20, 4, "global", None),
+    "metro_global_n2p20_y4": ("metropolis", 20, 4, "global", None),
+    "mego_smem_n2p14_y4": ("megopolis", 14, 4, "smem", None),
+    "mego_global_n2p24_y4": ("megopolis", 24, 4, "global", None),
+    "mego_gather6_n2p20_y2": ("megopolis", 20, 2, "global", "soa6"),
+    "bound_n2p20": ("bound", 20, 2, None, None),
+}
+
+
+def run_case(name: str):
+    """One named kernel case for profilers: three warm-up launches, then the
+    launch to capture (the fourth launch of the case's kernel)."""
+    import torch
+
+    import paper_2109_13504_gb300 as mego
+    import synthetic
+
+    kind, log2n, y, path, gather = PROFILE_CASES[name]
+    n = 1 << log2n
+    dev = torch.device("cuda:0")
+    w = torch.from_numpy(synthetic.gaussian_weights(n, y, SEED + y)).to(dev)
+    B_dev, status, _ = mego.mego_compute_B(w, EPS)
+    B = int(B_dev.item())
+    anc = torch.empty(n, dtype=torch.int32, device=dev)
+    x = x_out = None
+    if gather == "soa6":
+        x = torch.from_numpy(synthetic.gaussian_state(n, 6, SEED)).to(dev)
+        x_out = torch.empty_like(x)
+    for _ in range(4):
+        if kind == "bound":
+            mego.mego_compute_B(w, EPS, B_dev=B_dev, status=status)
+        else:
+            variant = mego.MEGOPOLIS if kind == "megopolis" else mego.METROPOLIS
+            cfg = {"path": mego.PATH_SMEM if path == "smem" else mego.PATH_GLOBAL}
+            mego.mego_resample_gather(w, B, None, SEED, 0, variant, x_in=x, x_out=x_out,
+                                      anc=anc, cfg=cfg)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": name, "n": n, "B": B}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -439,7 +510,12 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=1 << 20)
     ap.add_argument("--reference-sample", type=int, default=1 << 12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", choices=sorted(PROFILE_CASES),
+                    help="run one kernel case (for profilers) instead of the benchmark")
     args = ap.parse_args()
+    if args.case:
+        run_case(args.case)
+        return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

@@ -4,6 +4,7 @@
 // Deterministic: a fixed grid writes one partial (max, double sum, bad flag)
 // per CTA; a single CTA then folds the partials in index order.  The result
 // depends only on n and the weight bits.
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -20,11 +21,27 @@ struct Acc {
   double sum;
 };
 
-__device__ __forceinline__ void acc_add(Acc& a, float v) {
-  a.bad |= (!(v >= 0.0f) || isinf(v)) ? 1 : 0;
-  a.mx = fmaxf(a.mx, v);
-  a.sum += static_cast<double>(v);
-}
+// Per-thread accumulator: max, validity and a compensated (Neumaier) float
+// sum s + c, converted to double once per thread.  FP64 operations are slow
+// on this part, so none are used per element.  The compensated sum of a
+// thread's few thousand weights is exact to about 2 ulp of float squared.
+struct ThreadAcc {
+  float mx = 0.0f;
+  int bad = 0;
+  float s = 0.0f;
+  float c = 0.0f;
+  __device__ __forceinline__ void add(float v) {
+    bad |= (!(v >= 0.0f) || isinf(v)) ? 1 : 0;
+    mx = fmaxf(mx, v);
+    const float t = __fadd_rn(s, v);
+    c = __fadd_rn(c, fabsf(s) >= fabsf(v) ? __fadd_rn(__fsub_rn(s, t), v)
+                                            : __fadd_rn(__fsub_rn(v, t), s));
+    s = t;
+  }
+  __device__ __forceinline__ Acc to_acc() const {
+    return Acc{mx, bad, static_cast<double>(s) + static_cast<double>(c)};
+  }
+};
 
 __device__ __forceinline__ void acc_merge(Acc& a, const Acc& b) {
   a.bad |= b.bad;
@@ -64,10 +81,23 @@ __device__ __forceinline__ Acc block_reduce(Acc a) {
 // One partial per CTA.  LIKELIHOOD: src is state row 0 and the weight
 // w = exp(-(x - y)^2 / 2) is written to w_out before it is reduced.
 template <bool LIKELIHOOD>
+__device__ __forceinline__ float4 weight4(float4 v, float y, float4* w_out, uint32_t t) {
+  if constexpr (LIKELIHOOD) {
+    float d;
+    d = v.x - y; v.x = expf(-0.5f * d * d);
+    d = v.y - y; v.y = expf(-0.5f * d * d);
+    d = v.z - y; v.z = expf(-0.5f * d * d);
+    d = v.w - y; v.w = expf(-0.5f * d * d);
+    w_out[t] = v;
+  }
+  return v;
+}
+
+template <bool LIKELIHOOD>
 __global__ void __launch_bounds__(kReduceThreads)
 partials_kernel(const float* __restrict__ src, uint32_t n, float y,
                 float* __restrict__ w_out, Partial* __restrict__ parts) {
-  Acc a{0.0f, 0, 0.0};
+  ThreadAcc a;
   const uint32_t stride = gridDim.x * blockDim.x;
   const uint32_t t0 = blockIdx.x * blockDim.x + threadIdx.x;
   const bool vec = ((reinterpret_cast<uintptr_t>(src) & 15u) == 0u) &&
@@ -76,20 +106,27 @@ partials_kernel(const float* __restrict__ src, uint32_t n, float y,
   if (vec) {
     const uint32_t n4 = n / 4u;
     const float4* s4 = reinterpret_cast<const float4*>(src);
-    for (uint32_t t = t0; t < n4; t += stride) {
-      float4 v = __ldg(s4 + t);
-      if constexpr (LIKELIHOOD) {
-        float d;
-        d = v.x - y; v.x = expf(-0.5f * d * d);
-        d = v.y - y; v.y = expf(-0.5f * d * d);
-        d = v.z - y; v.z = expf(-0.5f * d * d);
-        d = v.w - y; v.w = expf(-0.5f * d * d);
-        reinterpret_cast<float4*>(w_out)[t] = v;
-      }
-      acc_add(a, v.x);
-      acc_add(a, v.y);
-      acc_add(a, v.z);
-      acc_add(a, v.w);
+    float4* w4 = reinterpret_cast<float4*>(w_out);
+    // Two independent loads in flight per thread before any accumulation.
+    uint32_t t = t0;
+    for (; t + stride < n4; t += 2u * stride) {
+      const float4 v0 = weight4<LIKELIHOOD>(__ldg(s4 + t), y, w4, t);
+      const float4 v1 = weight4<LIKELIHOOD>(__ldg(s4 + t + stride), y, w4, t + stride);
+      a.add(v0.x);
+      a.add(v0.y);
+      a.add(v0.z);
+      a.add(v0.w);
+      a.add(v1.x);
+      a.add(v1.y);
+      a.add(v1.z);
+      a.add(v1.w);
+    }
+    if (t < n4) {
+      const float4 v0 = weight4<LIKELIHOOD>(__ldg(s4 + t), y, w4, t);
+      a.add(v0.x);
+      a.add(v0.y);
+      a.add(v0.z);
+      a.add(v0.w);
     }
     tail = n4 * 4u;
   }
@@ -100,28 +137,38 @@ partials_kernel(const float* __restrict__ src, uint32_t n, float y,
       v = expf(-0.5f * d * d);
       w_out[i] = v;
     }
-    acc_add(a, v);
+    a.add(v);
   }
-  a = block_reduce(a);
-  if (threadIdx.x == 0) parts[blockIdx.x] = Partial{a.mx, a.bad, a.sum};
+  const Acc r = block_reduce(a.to_acc());
+  if (threadIdx.x == 0) parts[blockIdx.x] = Partial{r.mx, r.bad, r.sum};
 }
 
-__global__ void __launch_bounds__(kReduceThreads)
-finalize_kernel(const Partial* __restrict__ parts, int nparts, uint32_t n, double eps,
+__global__ void __launch_bounds__(32)
+finalize_kernel(const Partial* __restrict__ parts, int nparts, uint32_t n, double log_eps,
                 int32_t b_max, int32_t* __restrict__ d_B, int32_t* __restrict__ d_status,
                 double* __restrict__ d_q) {
+  // One warp: each lane folds its strided partials in index order, then a
+  // fixed shuffle tree combines the lanes.
   Acc a{0.0f, 0, 0.0};
-  for (int t = threadIdx.x; t < nparts; t += blockDim.x) {
+  for (int t = threadIdx.x; t < nparts; t += 32) {
     const Partial p = parts[t];
     acc_merge(a, Acc{p.mx, p.bad, p.sum});
   }
-  a = block_reduce(a);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    Acc o;
+    o.mx = __shfl_down_sync(0xFFFFFFFFu, a.mx, off);
+    o.bad = __shfl_down_sync(0xFFFFFFFFu, a.bad, off);
+    o.sum = __shfl_down_sync(0xFFFFFFFFu, a.sum, off);
+    acc_merge(a, o);
+  }
   if (threadIdx.x != 0) return;
   int32_t B = -1, status = kStatusWeights;
   double q = __longlong_as_double(0x7FF8000000000000LL);  // NaN
   if (!a.bad && a.mx > 0.0f) {
-    const double r = (a.sum / static_cast<double>(n)) / static_cast<double>(a.mx);
-    q = (r >= 1.0) ? 0.0 : log(eps) / log1p(-r);
+    // r = E(w) / max(w) with one division; log(eps) comes from the host.
+    const double r = a.sum / (static_cast<double>(n) * static_cast<double>(a.mx));
+    q = (r >= 1.0) ? 0.0 : log_eps / log1p(-r);
     double c = ceil(q);
     if (c < 0.0) c = 0.0;
     if (c <= static_cast<double>(b_max)) {
@@ -155,7 +202,7 @@ probe_read_kernel(const float4* __restrict__ buf, size_t n16, int reps,
 }  // namespace
 
 int reduce_grid(uint32_t n) {
-  const uint32_t per_cta = kReduceThreads * 8u;
+  const uint32_t per_cta = kReduceThreads * 16u;
   uint32_t g = (n + per_cta - 1u) / per_cta;
   if (g < 1u) g = 1u;
   if (g > static_cast<uint32_t>(kMaxParts)) g = kMaxParts;
@@ -175,8 +222,8 @@ cudaError_t launch_partials(const float* src, uint32_t n, bool likelihood, float
 cudaError_t launch_finalize(const Partial* parts, int nparts, uint32_t n, double eps,
                             int32_t b_max, int32_t* d_B, int32_t* d_status, double* d_q,
                             cudaStream_t st) {
-  finalize_kernel<<<1, kReduceThreads, 0, st>>>(parts, nparts, n, eps, b_max, d_B,
-                                                d_status, d_q);
+  finalize_kernel<<<1, 32, 0, st>>>(parts, nparts, n, std::log(eps), b_max, d_B, d_status,
+                                    d_q);
   return cudaGetLastError();
 }
 
