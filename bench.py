@@ -180,6 +180,73 @@ def _cpu_baseline(sample_particles: int):
                       "%.1f s of CPU work" % (sample_particles, N, t_total)}
 
 
+def _batched_leg(args, mego, synthetic, torch, dev):
+    """512 independent filters, N = floor(2^U[8,16]), y ~ U[0,4], B from the
+    bound at eps = 0.01: bound + Megopolis for all filters as one captured
+    CUDA graph (batched bound, one persistent resample launch) against the
+    same work as 512 separate mego_compute_B + mego_resample_gather calls."""
+    import statistics as stats
+    count = 512
+    sizes, ys = synthetic.filter_sizes(count, 8.0, 16.0, 4)
+    ws = [torch.from_numpy(synthetic.gaussian_weights(int(n), float(y), 40 + f)).to(dev)
+          for f, (n, y) in enumerate(zip(sizes, ys))]
+    ancs = [torch.empty(int(n), dtype=torch.int32, device=dev) for n in sizes]
+    filters = [{"w": w, "anc": a, "B": -1, "stream_id": f}
+               for f, (w, a) in enumerate(zip(ws, ancs))]
+    side = torch.cuda.Stream(dev)
+    total = int(sum(int(n) for n in sizes))
+    with torch.cuda.stream(side):
+        batch = mego.Batch(filters, seed=SEED, stream=side)
+        batch.bound(EPS, stream=side)
+        batch.resample(stream=side)
+        batch.autotune(reps=2, stream=side)
+        batch.capture(EPS, stream=side)
+        reps = max(5, args.steps // 4)
+        t_graph = []
+        for r in range(args.warmup + reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(side)
+            batch.replay(stream=side)
+            b.record(side)
+            side.synchronize()
+            if r >= args.warmup:
+                t_graph.append(a.elapsed_time(b))
+        Bs = batch.B.cpu().numpy()
+        # The same work as separate launches (bound + resample per filter).
+        wsp = torch.empty(mego.workspace_bytes(1 << 16), dtype=torch.uint8, device=dev)
+        B1 = torch.empty(1, dtype=torch.int32, device=dev)
+        s1 = torch.empty(1, dtype=torch.int32, device=dev)
+        q1 = torch.empty(1, dtype=torch.float64, device=dev)
+        t_sep = []
+        for r in range(args.warmup + max(3, reps // 4)):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(side)
+            for f in range(count):
+                mego.mego_compute_B(ws[f], EPS, B_dev=B1, status=s1, q=q1, ws=wsp, stream=side)
+                mego.mego_resample_gather(ws[f], 0, B1, SEED, f, mego.MEGOPOLIS, anc=ancs[f],
+                                          stream=side)
+            b.record(side)
+            side.synchronize()
+            if r >= args.warmup:
+                t_sep.append(a.elapsed_time(b))
+        shape = batch.shape
+        batch.close()
+
+    def pct(v, p):
+        v = sorted(v)
+        return v[min(len(v) - 1, int(round(p / 100.0 * (len(v) - 1))))]
+
+    return {"workload": "512 filters, N=floor(2^U[8,16]) (sum %d), y~U[0,4], Megopolis, "
+                        "B from Eq. 3 at eps=0.01 per filter (B from %d to %d)"
+                        % (total, int(Bs.min()), int(Bs.max())),
+            "graph_ms_p50": pct(t_graph, 50), "graph_ms_p99": pct(t_graph, 99),
+            "graph_particles_per_s": total / (stats.median(t_graph) / 1e3),
+            "separate_launches_ms_p50": pct(t_sep, 50),
+            "separate_particles_per_s": total / (stats.median(t_sep) / 1e3),
+            "speedup": stats.median(t_sep) / stats.median(t_graph),
+            "shape": shape}
+
+
 def run_reference(args):
     """The reference arm: the CPU oracle as it stands, timed on the host."""
     world, rank, _ = _dist()
@@ -386,6 +453,8 @@ def run_gpu(args):
     e2e_s = time.perf_counter() - t0
     e2e_value = N * len(YS) * e2e_steps / e2e_s
 
+    batched = _batched_leg(args, mego, synthetic, torch, dev)
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -447,6 +516,7 @@ def run_gpu(args):
                                      "frac_of_hbm": achieved_gbs / hbm_peak,
                                      "l2_probe_gbs": l2_best,
                                      "frac_of_l2_probe": achieved_gbs / l2_best}},
+        "batched": batched,
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": 4 * N * len(YS),

@@ -200,6 +200,76 @@ mego_status mego_resample_host(const float* h_w, int32_t n, int32_t B,
                                void* d_ws, size_t ws_bytes, void* stream);
 
 /* ----------------------------------------------------------------------
+ * Batched resampling: many independent problems ("filters") of uneven size
+ * in one persistent launch.  (The paper resamples one filter at a time; the
+ * batch runs Algorithm 5 or Algorithm 2 on each filter unchanged.)
+ *
+ * One seed per batch; each filter has its own stream id, so a filter's
+ * ancestors equal those of mego_resample_gather with the same seed, stream
+ * id and B, whatever else is in the batch.
+ *
+ * Plan: mego_batch_plan copies per-filter descriptors and work-item tables
+ * into a caller-provided device buffer of mego_batch_plan_bytes() bytes
+ * (256-byte aligned) and fills the host handle *out.  Filters' buffers are
+ * the caller's and must stay valid while the plan is used.  A plan must not
+ * be launched twice concurrently (its work queue is shared).
+ * Bound: mego_batch_bound computes each filter's B (Eq. 3) into the plan
+ * (out->d_B, out->d_status, out->d_q: int32, int32, double per filter);
+ * filters whose descriptor has B < 0 use it.  Resample: one persistent
+ * kernel, warps taking (filter, 128-particle) work items from a queue.
+ * Graph: mego_batch_graph captures [bound (if eps > 0)] + resample into a
+ * CUDA graph held by the handle (needs a non-default stream); replay with
+ * mego_batch_launch_graph; mego_batch_destroy releases it.
+ * Only MEGO_MEGOPOLIS and MEGO_METROPOLIS; the global-memory path; all
+ * filters of a batch gather with the same layout, or none does.
+ */
+typedef struct mego_filter {
+  const float* w;      /* [n] weights (device)                                */
+  int32_t* anc;        /* [n] ancestors (device), may be NULL when gathering  */
+  const float* x_in;   /* state in the batch layout (device) or NULL          */
+  float* x_out;        /* gathered state (device) or NULL                     */
+  int64_t ld;          /* SoA row stride in floats (>= n)                     */
+  int32_t n;           /* 1..MEGO_N_MAX                                       */
+  int32_t B;           /* iterations, or < 0 for the batch bound's value      */
+  uint32_t stream_id;  /* random stream of this filter                        */
+  int32_t dim;         /* SoA rows to gather; 4 for AoS4                      */
+} mego_filter;
+
+typedef struct mego_batch {
+  void* d_plan;
+  size_t plan_bytes;
+  int32_t count, variant, layout, gather;
+  uint64_t seed;
+  uint64_t total_items, total_chunks;
+  int32_t* d_B;        /* [count] per-filter bound (device, inside the plan)  */
+  int32_t* d_status;   /* [count] per-filter status                           */
+  double* d_q;         /* [count] per-filter value before the ceiling         */
+  mego_launch_cfg cfg; /* threads and particles per thread of the launch      */
+  int32_t grid;
+  void* graph_exec;    /* captured graph, or NULL                             */
+} mego_batch;
+
+size_t mego_batch_plan_bytes(const mego_filter* h_filters, int32_t count);
+mego_status mego_batch_plan(const mego_filter* h_filters, int32_t count,
+                            int variant, int layout, uint64_t seed,
+                            void* d_plan, size_t plan_bytes, mego_batch* out,
+                            void* stream);
+mego_status mego_batch_bound(const mego_batch* b, double eps, int32_t b_max,
+                             void* stream);
+mego_status mego_batch_resample(const mego_batch* b, void* stream);
+/* Shape of the persistent launch (threads 64..256, particles per thread
+ * 1, 2 or 4); the grid is always SMs x resident CTAs. */
+mego_status mego_batch_set_shape(mego_batch* b, int32_t threads, int32_t ppt);
+/* Time every shape on the batch as planned (outputs are overwritten) and
+ * keep the fastest. */
+mego_status mego_batch_autotune(mego_batch* b, int32_t reps, float* best_ms,
+                                void* stream);
+mego_status mego_batch_graph(mego_batch* b, double eps, int32_t b_max,
+                             void* stream);
+mego_status mego_batch_launch_graph(const mego_batch* b, void* stream);
+mego_status mego_batch_destroy(mego_batch* b);
+
+/* ----------------------------------------------------------------------
  * Wait for `stream` up to timeout_s seconds by polling an event, then copy
  * the device status word to *h_status.  Returns MEGO_ETIMEOUT (and leaves
  * *h_status untouched) if the stream has not drained by the deadline. */

@@ -58,6 +58,22 @@ class LaunchCfg(ctypes.Structure):
                 ("path", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
 
 
+class Filter(ctypes.Structure):
+    _fields_ = [("w", ctypes.c_void_p), ("anc", ctypes.c_void_p), ("x_in", ctypes.c_void_p),
+                ("x_out", ctypes.c_void_p), ("ld", ctypes.c_int64), ("n", ctypes.c_int32),
+                ("B", ctypes.c_int32), ("stream_id", ctypes.c_uint32), ("dim", ctypes.c_int32)]
+
+
+class BatchHandle(ctypes.Structure):
+    _fields_ = [("d_plan", ctypes.c_void_p), ("plan_bytes", ctypes.c_size_t),
+                ("count", ctypes.c_int32), ("variant", ctypes.c_int32),
+                ("layout", ctypes.c_int32), ("gather", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("total_items", ctypes.c_uint64),
+                ("total_chunks", ctypes.c_uint64), ("d_B", ctypes.c_void_p),
+                ("d_status", ctypes.c_void_p), ("d_q", ctypes.c_void_p),
+                ("cfg", LaunchCfg), ("grid", ctypes.c_int32), ("graph_exec", ctypes.c_void_p)]
+
+
 _lib = None
 
 
@@ -90,6 +106,17 @@ def _load():
                                 sz, vp], ci),
         "mego_sync_status": ([vp, vp, f64, vp], ci),
         "mego_probe_read": ([vp, sz, i32, vp, vp], ci),
+        "mego_batch_plan_bytes": ([ctypes.POINTER(Filter), i32], sz),
+        "mego_batch_plan": ([ctypes.POINTER(Filter), i32, ci, ci, u64, vp, sz,
+                             ctypes.POINTER(BatchHandle), vp], ci),
+        "mego_batch_bound": ([ctypes.POINTER(BatchHandle), f64, i32, vp], ci),
+        "mego_batch_resample": ([ctypes.POINTER(BatchHandle), vp], ci),
+        "mego_batch_set_shape": ([ctypes.POINTER(BatchHandle), i32, i32], ci),
+        "mego_batch_autotune": ([ctypes.POINTER(BatchHandle), i32,
+                                 ctypes.POINTER(ctypes.c_float), vp], ci),
+        "mego_batch_graph": ([ctypes.POINTER(BatchHandle), f64, i32, vp], ci),
+        "mego_batch_launch_graph": ([ctypes.POINTER(BatchHandle), vp], ci),
+        "mego_batch_destroy": ([ctypes.POINTER(BatchHandle)], ci),
         "mego_autotune": ([vp, i32, i32, ci, u32, vp, vp, i32, ctypes.c_int64, ci, vp, i32,
                            ctypes.POINTER(LaunchCfg), ctypes.POINTER(ctypes.c_float), vp], ci),
     }
@@ -363,3 +390,114 @@ def resample(w: torch.Tensor, B: Optional[int] = None, eps: float = 0.01, seed: 
         mego_resample_gather(w, int(B), None, seed, stream_id, variant, psize_bytes, anc=anc,
                              cfg=cfg, stream=stream)
     return anc
+
+
+# --------------------------------------------------------------------------
+# Batched resampling
+
+
+class Batch:
+    """Many independent filters resampled by one persistent launch.
+
+    filters: list of dicts with keys w (CUDA float32 [n]), anc (CUDA int32
+    [n], optional when gathering), x_in/x_out (optional state), B (int, or
+    -1 to use the batch bound), stream_id (int).  The tensors must stay alive
+    while the batch is used; the Batch keeps references to them.
+    """
+
+    def __init__(self, filters, variant: int = MEGOPOLIS, layout: int = LAYOUT_SOA,
+                 seed: int = 0, stream=None):
+        lib = _load()
+        self._keep = filters
+        self.count = len(filters)
+        arr = (Filter * self.count)()
+        dev = None
+        for f, d in enumerate(filters):
+            w = d["w"]
+            dev = w.device
+            n = w.numel()
+            x_in, x_out = d.get("x_in"), d.get("x_out")
+            dim, ld = 0, 0
+            if x_in is not None:
+                if layout == LAYOUT_SOA:
+                    dim, ld = x_in.shape[0], x_in.shape[1]
+                else:
+                    dim, ld = 4, 4
+            anc = d.get("anc")
+            arr[f] = Filter(_dev(w, torch.float32, "w"),
+                            _dev(anc, torch.int32, "anc", n) if anc is not None else None,
+                            _dev(x_in, torch.float32, "x_in") if x_in is not None else None,
+                            _dev(x_out, torch.float32, "x_out") if x_out is not None else None,
+                            int(ld), int(n), int(d.get("B", -1)), int(d.get("stream_id", f)),
+                            int(dim))
+        self._filters = arr
+        nbytes = int(lib.mego_batch_plan_bytes(arr, self.count))
+        if nbytes == 0:
+            raise MegoError(MEGO_EINVAL, "mego_batch_plan_bytes")
+        self.plan = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        self.handle = BatchHandle()
+        st = lib.mego_batch_plan(arr, self.count, int(variant), int(layout), int(seed),
+                                 self.plan.data_ptr(), nbytes, ctypes.byref(self.handle),
+                                 _stream(stream))
+        _check(st, "mego_batch_plan")
+
+    def _view(self, ptr, dtype, numel):
+        off = int(ptr) - self.plan.data_ptr()
+        esz = torch.empty(0, dtype=dtype).element_size()
+        return self.plan[off:off + esz * numel].view(dtype)
+
+    @property
+    def B(self) -> torch.Tensor:
+        return self._view(self.handle.d_B, torch.int32, self.count)
+
+    @property
+    def status(self) -> torch.Tensor:
+        return self._view(self.handle.d_status, torch.int32, self.count)
+
+    @property
+    def q(self) -> torch.Tensor:
+        return self._view(self.handle.d_q, torch.float64, self.count)
+
+    def bound(self, eps: float = 0.01, b_max: int = B_MAX, stream=None):
+        _check(_load().mego_batch_bound(ctypes.byref(self.handle), float(eps), int(b_max),
+                                        _stream(stream)), "mego_batch_bound")
+
+    def resample(self, stream=None):
+        _check(_load().mego_batch_resample(ctypes.byref(self.handle), _stream(stream)),
+               "mego_batch_resample")
+
+    def set_shape(self, threads: int, ppt: int):
+        _check(_load().mego_batch_set_shape(ctypes.byref(self.handle), int(threads), int(ppt)),
+               "mego_batch_set_shape")
+
+    def autotune(self, reps: int = 3, stream=None) -> float:
+        ms = ctypes.c_float()
+        _check(_load().mego_batch_autotune(ctypes.byref(self.handle), int(reps),
+                                           ctypes.byref(ms), _stream(stream)),
+               "mego_batch_autotune")
+        return float(ms.value)
+
+    @property
+    def shape(self):
+        return {"threads": self.handle.cfg.threads, "ppt": self.handle.cfg.ppt,
+                "grid": self.handle.grid}
+
+    def capture(self, eps: float = 0.01, b_max: int = B_MAX, stream=None):
+        """Capture [bound if eps > 0] + resample into a CUDA graph (needs a
+        non-default stream)."""
+        _check(_load().mego_batch_graph(ctypes.byref(self.handle), float(eps), int(b_max),
+                                        _stream(stream)), "mego_batch_graph")
+
+    def replay(self, stream=None):
+        _check(_load().mego_batch_launch_graph(ctypes.byref(self.handle), _stream(stream)),
+               "mego_batch_launch_graph")
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and _lib is not None:
+            _lib.mego_batch_destroy(ctypes.byref(self.handle))
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,607 @@
+// batch.cu -- many independent resampling problems ("filters") in one
+// persistent launch.
+//
+// Plan (a caller-provided device buffer, written by mego_batch_plan):
+//   header (queue counters, counts) | filter descriptors | item prefix sums |
+//   chunk prefix sums | per-filter B, status, q | bound partials.
+// Resample work items are (filter, 4 consecutive 32-particle segments);
+// warps of a persistent grid take items from a queue (one atomic per item),
+// so filters of very different cost (size times B) balance themselves.  The
+// last warp to leave resets the queue, so the plan can be launched again.
+// The bound runs one CTA per (filter, 4096-weight chunk) and one warp per
+// filter for the fold, in fixed order (deterministic).
+// One seed per batch; every filter has its own stream id, so a filter's
+// ancestors are the same alone (mego_resample_gather with that seed and
+// stream id) and in any batch.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/megopolis.h"
+#include "bound.cuh"
+#include "resample_kernels.cuh"
+
+namespace mego {
+namespace {
+
+constexpr uint32_t kItemSegs = 4;        // segments (32 particles each) per work item
+constexpr uint32_t kChunk = 4096;        // weights per bound work item
+constexpr int kBoundThreads = 256;       // 16 weights per thread per chunk
+
+struct FilterDev {
+  const float* w;
+  int32_t* anc;
+  const float* x_in;
+  float* x_out;
+  int64_t ld;
+  uint32_t n;
+  int32_t B;        // >= 0: fixed; < 0: the batch bound's value
+  uint32_t sid;
+  int32_t dim;
+};
+
+struct PlanHeader {
+  uint32_t next;         // resample queue head
+  uint32_t done;         // warps that left the resample kernel
+  uint32_t count;
+  uint32_t total_items;
+  uint32_t total_chunks;
+  uint32_t pad[3];
+};
+
+struct PlanLayout {
+  size_t filters, item_prefix, chunk_prefix, B, status, q, parts, total;
+};
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+PlanLayout layout_for(uint32_t count, uint64_t total_chunks) {
+  PlanLayout L;
+  size_t off = sizeof(PlanHeader);
+  off = align_up(off, 16);
+  L.filters = off;
+  off += sizeof(FilterDev) * count;
+  off = align_up(off, 16);
+  L.item_prefix = off;
+  off += sizeof(uint32_t) * (count + 1);
+  off = align_up(off, 16);
+  L.chunk_prefix = off;
+  off += sizeof(uint32_t) * (count + 1);
+  off = align_up(off, 16);
+  L.B = off;
+  off += sizeof(int32_t) * count;
+  off = align_up(off, 16);
+  L.status = off;
+  off += sizeof(int32_t) * count;
+  off = align_up(off, 16);
+  L.q = off;
+  off += sizeof(double) * count;
+  off = align_up(off, 16);
+  L.parts = off;
+  off += sizeof(Partial) * total_chunks;
+  L.total = align_up(off, 256);
+  return L;
+}
+
+struct BatchArgs {
+  unsigned char* plan;
+  size_t off_filters, off_item_prefix, off_chunk_prefix, off_B, off_status, off_q, off_parts;
+  RoundKeys K;
+};
+
+// Largest f with prefix[f] <= x (prefix non-decreasing, prefix[0] = 0).
+__device__ __forceinline__ uint32_t find_owner(const uint32_t* prefix, uint32_t count,
+                                               uint32_t x) {
+  uint32_t lo = 0, hi = count;  // answer in [lo, hi)
+  while (hi - lo > 1u) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (__ldg(prefix + mid) <= x) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------
+// Bound: partial per (filter, chunk), then one warp per filter.
+
+struct BAcc {
+  float mx = 0.0f;
+  int bad = 0;
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float v) {
+    bad |= (!(v >= 0.0f) || isinf(v)) ? 1 : 0;
+    mx = fmaxf(mx, v);
+    const float t = __fadd_rn(s, v);
+    c = __fadd_rn(c, fabsf(s) >= fabsf(v) ? __fadd_rn(__fsub_rn(s, t), v)
+                                            : __fadd_rn(__fsub_rn(v, t), s));
+    s = t;
+  }
+};
+
+__global__ void __launch_bounds__(kBoundThreads) batch_partials_kernel(const __grid_constant__ BatchArgs a) {
+  const PlanHeader* h = reinterpret_cast<const PlanHeader*>(a.plan);
+  const FilterDev* F = reinterpret_cast<const FilterDev*>(a.plan + a.off_filters);
+  const uint32_t* cp = reinterpret_cast<const uint32_t*>(a.plan + a.off_chunk_prefix);
+  Partial* parts = reinterpret_cast<Partial*>(a.plan + a.off_parts);
+  const uint32_t count = h->count;
+  const uint32_t chunk = blockIdx.x;
+  const uint32_t f = find_owner(cp, count, chunk);
+  const uint32_t n = F[f].n;
+  const float* w = F[f].w;
+  const uint32_t lo = (chunk - cp[f]) * kChunk;
+  const uint32_t hi = min(n, lo + kChunk);
+  BAcc acc;
+  for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) acc.add(__ldg(w + i));
+  // Fixed-order tree: warp shuffles, then warp 0 over the warp results.
+  double sum = static_cast<double>(acc.s) + static_cast<double>(acc.c);
+  float mx = acc.mx;
+  int bad = acc.bad;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    sum += __shfl_down_sync(0xFFFFFFFFu, sum, off);
+    mx = fmaxf(mx, __shfl_down_sync(0xFFFFFFFFu, mx, off));
+    bad |= __shfl_down_sync(0xFFFFFFFFu, bad, off);
+  }
+  __shared__ double s_sum[kBoundThreads / 32];
+  __shared__ float s_mx[kBoundThreads / 32];
+  __shared__ int s_bad[kBoundThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    s_sum[warp] = sum;
+    s_mx[warp] = mx;
+    s_bad[warp] = bad;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    float m = 0.0f;
+    int b = 0;
+    for (int k = 0; k < kBoundThreads / 32; ++k) {
+      t += s_sum[k];
+      m = fmaxf(m, s_mx[k]);
+      b |= s_bad[k];
+    }
+    parts[chunk] = Partial{m, b, t};
+  }
+}
+
+__global__ void __launch_bounds__(256) batch_finalize_kernel(const __grid_constant__ BatchArgs a,
+                                                             double log_eps, int32_t b_max) {
+  const PlanHeader* h = reinterpret_cast<const PlanHeader*>(a.plan);
+  const FilterDev* F = reinterpret_cast<const FilterDev*>(a.plan + a.off_filters);
+  const uint32_t* cp = reinterpret_cast<const uint32_t*>(a.plan + a.off_chunk_prefix);
+  const Partial* parts = reinterpret_cast<const Partial*>(a.plan + a.off_parts);
+  int32_t* Bout = reinterpret_cast<int32_t*>(a.plan + a.off_B);
+  int32_t* Sout = reinterpret_cast<int32_t*>(a.plan + a.off_status);
+  double* Qout = reinterpret_cast<double*>(a.plan + a.off_q);
+  const uint32_t f = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const uint32_t lane = threadIdx.x & 31u;
+  if (f >= h->count) return;
+  double sum = 0.0;
+  float mx = 0.0f;
+  int bad = 0;
+  for (uint32_t c = cp[f] + lane; c < cp[f + 1]; c += 32u) {
+    const Partial p = parts[c];
+    sum += p.sum;
+    mx = fmaxf(mx, p.mx);
+    bad |= p.bad;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    sum += __shfl_down_sync(0xFFFFFFFFu, sum, off);
+    mx = fmaxf(mx, __shfl_down_sync(0xFFFFFFFFu, mx, off));
+    bad |= __shfl_down_sync(0xFFFFFFFFu, bad, off);
+  }
+  if (lane != 0) return;
+  int32_t B = -1, status = kStatusWeights;
+  double q = __longlong_as_double(0x7FF8000000000000LL);
+  if (!bad && mx > 0.0f) {
+    const double r = sum / (static_cast<double>(F[f].n) * static_cast<double>(mx));
+    q = (r >= 1.0) ? 0.0 : log_eps / log1p(-r);
+    double c = ceil(q);
+    if (c < 0.0) c = 0.0;
+    if (c <= static_cast<double>(b_max)) {
+      B = static_cast<int32_t>(c);
+      status = 0;
+    }
+  }
+  Bout[f] = B;
+  Sout[f] = status;
+  Qout[f] = q;
+}
+
+// ---------------------------------------------------------------------------
+// Persistent resample over the work queue.
+
+template <int VARIANT, int P, int GATHER>
+__global__ void __launch_bounds__(256) batch_resample_kernel(const __grid_constant__ BatchArgs a) {
+  __shared__ int2 s_win[kMaxWarps][32];
+  PlanHeader* h = reinterpret_cast<PlanHeader*>(a.plan);
+  const FilterDev* F = reinterpret_cast<const FilterDev*>(a.plan + a.off_filters);
+  const uint32_t* ip = reinterpret_cast<const uint32_t*>(a.plan + a.off_item_prefix);
+  const int32_t* Bb = reinterpret_cast<const int32_t*>(a.plan + a.off_B);
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t count = h->count;
+  const uint32_t total = h->total_items;
+  int2* win = s_win[threadIdx.x >> 5];
+  for (;;) {
+    uint32_t item = 0;
+    if (lane == 0) item = atomicAdd(&h->next, 1u);
+    item = __shfl_sync(0xFFFFFFFFu, item, 0);
+    if (item >= total) break;
+    const uint32_t f = find_owner(ip, count, item);
+    const FilterDev d = F[f];
+    const int B = d.B >= 0 ? d.B : Bb[f];
+    if (B < 0) continue;  // the bound failed for this filter: write nothing
+    Problem p;
+    p.w = d.w;
+    p.anc = d.anc;
+    p.x_in = d.x_in;
+    p.x_out = d.x_out;
+    p.fault = nullptr;
+    p.ld = d.ld;
+    p.n = d.n;
+    p.nseg = (d.n + 31u) / 32u;
+    p.dim = d.dim;
+    p.nw = 1u;
+    p.npart = d.n;
+    p.S = stream_key(a.K, d.sid);
+    const uint32_t seg_lo = (item - ip[f]) * kItemSegs;
+    const uint32_t seg_hi = min(p.nseg, seg_lo + kItemSegs);
+    run_segments<VARIANT, P, false, GATHER>(p, a.K, B, seg_lo, seg_hi, lane, win);
+  }
+  // The last warp out resets the queue for the next launch of this plan.
+  if (lane == 0) {
+    __threadfence();
+    const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+    if (atomicAdd(&h->done, 1u) == warps - 1u) {
+      h->next = 0u;
+      h->done = 0u;
+      __threadfence();
+    }
+  }
+}
+
+template <int V, int P, int G>
+cudaError_t launch_batch_one(int grid, int threads, const BatchArgs& a, cudaStream_t st) {
+  batch_resample_kernel<V, P, G><<<grid, threads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int V, int P, int G>
+const void* batch_ptr_one() {
+  return reinterpret_cast<const void*>(&batch_resample_kernel<V, P, G>);
+}
+
+template <int V, int G>
+cudaError_t launch_batch_p(int ppt, int grid, int threads, const BatchArgs& a, cudaStream_t st) {
+  switch (ppt) {
+    case 1: return launch_batch_one<V, 1, G>(grid, threads, a, st);
+    case 2: return launch_batch_one<V, 2, G>(grid, threads, a, st);
+    case 4: return launch_batch_one<V, 4, G>(grid, threads, a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int V, int G>
+const void* batch_ptr_p(int ppt) {
+  switch (ppt) {
+    case 1: return batch_ptr_one<V, 1, G>();
+    case 2: return batch_ptr_one<V, 2, G>();
+    case 4: return batch_ptr_one<V, 4, G>();
+    default: return nullptr;
+  }
+}
+
+template <int V>
+cudaError_t launch_batch_v(int gather, int ppt, int grid, int threads, const BatchArgs& a,
+                           cudaStream_t st) {
+  switch (gather) {
+    case kGatherNone: return launch_batch_p<V, kGatherNone>(ppt, grid, threads, a, st);
+    case kGatherSoa: return launch_batch_p<V, kGatherSoa>(ppt, grid, threads, a, st);
+    case kGatherAos4: return launch_batch_p<V, kGatherAos4>(ppt, grid, threads, a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int V>
+const void* batch_ptr_v(int gather, int ppt) {
+  switch (gather) {
+    case kGatherNone: return batch_ptr_p<V, kGatherNone>(ppt);
+    case kGatherSoa: return batch_ptr_p<V, kGatherSoa>(ppt);
+    case kGatherAos4: return batch_ptr_p<V, kGatherAos4>(ppt);
+    default: return nullptr;
+  }
+}
+
+const void* batch_kernel_ptr(int variant, int gather, int ppt) {
+  return variant == MEGO_MEGOPOLIS ? batch_ptr_v<kMegopolis>(gather, ppt)
+                                   : batch_ptr_v<kMetropolis>(gather, ppt);
+}
+
+cudaError_t launch_batch(int variant, int gather, int ppt, int grid, int threads,
+                         const BatchArgs& a, cudaStream_t st) {
+  return variant == MEGO_MEGOPOLIS
+             ? launch_batch_v<kMegopolis>(gather, ppt, grid, threads, a, st)
+             : launch_batch_v<kMetropolis>(gather, ppt, grid, threads, a, st);
+}
+
+int gather_of(int layout, bool has_state) {
+  if (!has_state) return kGatherNone;
+  return layout == MEGO_LAYOUT_AOS4 ? kGatherAos4 : kGatherSoa;
+}
+
+BatchArgs args_of(const mego_batch* b) {
+  BatchArgs a;
+  std::memset(&a, 0, sizeof a);
+  const PlanLayout L = layout_for(static_cast<uint32_t>(b->count), b->total_chunks);
+  a.plan = static_cast<unsigned char*>(b->d_plan);
+  a.off_filters = L.filters;
+  a.off_item_prefix = L.item_prefix;
+  a.off_chunk_prefix = L.chunk_prefix;
+  a.off_B = L.B;
+  a.off_status = L.status;
+  a.off_q = L.q;
+  a.off_parts = L.parts;
+  a.K = make_round_keys(b->seed);
+  return a;
+}
+
+// Grid of the persistent kernel: every SM full of resident CTAs.
+mego_status shape_for(int variant, int gather, int threads, int ppt, int* grid) {
+  const void* k = batch_kernel_ptr(variant, gather, ppt);
+  if (!k) return MEGO_EINVAL;
+  int dev = 0, sms = 0, occ = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MEGO_ECUDA;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return MEGO_ECUDA;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, threads, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return MEGO_ECUDA;
+  }
+  if (occ < 1) return MEGO_EINVAL;
+  *grid = sms * occ;
+  return MEGO_OK;
+}
+
+bool sizes(const mego_filter* h, int32_t count, uint64_t* items, uint64_t* chunks) {
+  uint64_t it = 0, ch = 0;
+  for (int32_t f = 0; f < count; ++f) {
+    if (h[f].n < 1 || h[f].n > MEGO_N_MAX) return false;
+    const uint64_t nseg = (static_cast<uint64_t>(h[f].n) + 31u) / 32u;
+    it += (nseg + kItemSegs - 1) / kItemSegs;
+    ch += (static_cast<uint64_t>(h[f].n) + kChunk - 1) / kChunk;
+  }
+  if (it >= (1ull << 31) || ch >= (1ull << 31)) return false;
+  *items = it;
+  *chunks = ch;
+  return true;
+}
+
+}  // namespace
+}  // namespace mego
+
+extern "C" {
+
+size_t mego_batch_plan_bytes(const mego_filter* h_filters, int32_t count) {
+  uint64_t items = 0, chunks = 0;
+  if (!h_filters || count < 1 || !mego::sizes(h_filters, count, &items, &chunks)) return 0;
+  return mego::layout_for(static_cast<uint32_t>(count), chunks).total;
+}
+
+mego_status mego_batch_plan(const mego_filter* h_filters, int32_t count, int variant,
+                            int layout, uint64_t seed, void* d_plan, size_t plan_bytes,
+                            mego_batch* out, void* stream) {
+  using namespace mego;
+  if (!h_filters || count < 1 || !d_plan || !out) return MEGO_EINVAL;
+  if (variant != MEGO_MEGOPOLIS && variant != MEGO_METROPOLIS) return MEGO_EINVAL;
+  if (layout != MEGO_LAYOUT_SOA && layout != MEGO_LAYOUT_AOS4) return MEGO_EINVAL;
+  if (reinterpret_cast<uintptr_t>(d_plan) & 255u) return MEGO_EINVAL;
+  uint64_t items = 0, chunks = 0;
+  if (!sizes(h_filters, count, &items, &chunks)) return MEGO_EINVAL;
+  const PlanLayout L = layout_for(static_cast<uint32_t>(count), chunks);
+  if (plan_bytes < L.total) return MEGO_ENOMEM;
+  bool has_state = false, no_state = false;
+  for (int32_t f = 0; f < count; ++f) {
+    const mego_filter& d = h_filters[f];
+    if (!d.w || d.B > MEGO_B_MAX) return MEGO_EINVAL;
+    const bool st = d.x_in || d.x_out;
+    if (st) {
+      if (!d.x_in || !d.x_out) return MEGO_EINVAL;
+      if (layout == MEGO_LAYOUT_SOA && (d.dim < 1 || d.ld < d.n)) return MEGO_EINVAL;
+      if (layout == MEGO_LAYOUT_AOS4 &&
+          (d.dim != 4 ||
+           ((reinterpret_cast<uintptr_t>(d.x_in) | reinterpret_cast<uintptr_t>(d.x_out)) & 15u)))
+        return MEGO_EINVAL;
+      has_state = true;
+    } else {
+      if (!d.anc) return MEGO_EINVAL;
+      no_state = true;
+    }
+  }
+  if (has_state && no_state) return MEGO_EINVAL;  // one gather layout per batch
+  std::vector<unsigned char> host(L.parts, 0);
+  PlanHeader hdr{};
+  hdr.count = static_cast<uint32_t>(count);
+  hdr.total_items = static_cast<uint32_t>(items);
+  hdr.total_chunks = static_cast<uint32_t>(chunks);
+  std::memcpy(host.data(), &hdr, sizeof hdr);
+  FilterDev* F = reinterpret_cast<FilterDev*>(host.data() + L.filters);
+  uint32_t* ip = reinterpret_cast<uint32_t*>(host.data() + L.item_prefix);
+  uint32_t* cp = reinterpret_cast<uint32_t*>(host.data() + L.chunk_prefix);
+  int32_t* Bv = reinterpret_cast<int32_t*>(host.data() + L.B);
+  uint64_t it = 0, ch = 0;
+  for (int32_t f = 0; f < count; ++f) {
+    const mego_filter& d = h_filters[f];
+    F[f] = FilterDev{d.w, d.anc, d.x_in, d.x_out, d.ld, static_cast<uint32_t>(d.n), d.B,
+                     d.stream_id, d.dim};
+    ip[f] = static_cast<uint32_t>(it);
+    cp[f] = static_cast<uint32_t>(ch);
+    Bv[f] = d.B;
+    const uint64_t nseg = (static_cast<uint64_t>(d.n) + 31u) / 32u;
+    it += (nseg + kItemSegs - 1) / kItemSegs;
+    ch += (static_cast<uint64_t>(d.n) + kChunk - 1) / kChunk;
+  }
+  ip[count] = static_cast<uint32_t>(it);
+  cp[count] = static_cast<uint32_t>(ch);
+  if (cudaMemcpyAsync(d_plan, host.data(), host.size(), cudaMemcpyHostToDevice,
+                      static_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return MEGO_ECUDA;
+  // The copy reads `host` before cudaMemcpyAsync returns (pageable source).
+  std::memset(out, 0, sizeof *out);
+  out->d_plan = d_plan;
+  out->plan_bytes = L.total;
+  out->count = count;
+  out->variant = variant;
+  out->layout = layout;
+  out->gather = gather_of(layout, has_state);
+  out->seed = seed;
+  out->total_items = items;
+  out->total_chunks = chunks;
+  out->d_B = reinterpret_cast<int32_t*>(static_cast<unsigned char*>(d_plan) + L.B);
+  out->d_status = reinterpret_cast<int32_t*>(static_cast<unsigned char*>(d_plan) + L.status);
+  out->d_q = reinterpret_cast<double*>(static_cast<unsigned char*>(d_plan) + L.q);
+  out->cfg.threads = 256;
+  out->cfg.ppt = 2;
+  out->cfg.path = MEGO_PATH_GLOBAL;
+  out->cfg.ctas_per_sm = 0;
+  int grid = 0;
+  const mego_status s = shape_for(variant, out->gather, 256, 2, &grid);
+  if (s != MEGO_OK) return s;
+  out->grid = grid;
+  return MEGO_OK;
+}
+
+mego_status mego_batch_bound(const mego_batch* b, double eps, int32_t b_max, void* stream) {
+  using namespace mego;
+  if (!b || !b->d_plan || !(eps > 0.0 && eps <= 1.0) || b_max < 1 || b_max > MEGO_B_MAX)
+    return MEGO_EINVAL;
+  const BatchArgs a = args_of(b);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  batch_partials_kernel<<<static_cast<unsigned>(b->total_chunks), kBoundThreads, 0, st>>>(a);
+  if (cudaGetLastError() != cudaSuccess) return MEGO_ECUDA;
+  const unsigned fgrid = static_cast<unsigned>((b->count + 7) / 8);
+  batch_finalize_kernel<<<fgrid, 256, 0, st>>>(a, std::log(eps), b_max);
+  if (cudaGetLastError() != cudaSuccess) return MEGO_ECUDA;
+  return MEGO_OK;
+}
+
+mego_status mego_batch_resample(const mego_batch* b, void* stream) {
+  using namespace mego;
+  if (!b || !b->d_plan || b->grid < 1) return MEGO_EINVAL;
+  const BatchArgs a = args_of(b);
+  if (launch_batch(b->variant, b->gather, b->cfg.ppt, b->grid, b->cfg.threads, a,
+                   static_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return MEGO_ECUDA;
+  return MEGO_OK;
+}
+
+mego_status mego_batch_set_shape(mego_batch* b, int32_t threads, int32_t ppt) {
+  using namespace mego;
+  if (!b || threads < 64 || threads > 256 || threads % 32 || (ppt != 1 && ppt != 2 && ppt != 4))
+    return MEGO_EINVAL;
+  int grid = 0;
+  const mego_status s = shape_for(b->variant, b->gather, threads, ppt, &grid);
+  if (s != MEGO_OK) return s;
+  b->cfg.threads = threads;
+  b->cfg.ppt = ppt;
+  b->grid = grid;
+  return MEGO_OK;
+}
+
+mego_status mego_batch_autotune(mego_batch* b, int32_t reps, float* best_ms, void* stream) {
+  if (!b || reps < 1 || reps > 100) return MEGO_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return MEGO_ECUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return MEGO_ECUDA;
+  }
+  const int threads_c[] = {64, 128, 256};
+  const int ppt_c[] = {1, 2, 4};
+  int best_t = b->cfg.threads, best_p = b->cfg.ppt;
+  float best = 1e30f;
+  mego_status status = MEGO_OK;
+  for (int t : threads_c) {
+    for (int p : ppt_c) {
+      mego_status s = mego_batch_set_shape(b, t, p);
+      if (s == MEGO_EINVAL) continue;
+      if (s == MEGO_OK) s = mego_batch_resample(b, stream);  // warm-up
+      float total = 0.0f;
+      for (int r = 0; r < reps && s == MEGO_OK; ++r) {
+        float ms = 0.0f;
+        if (cudaEventRecord(e0, st) != cudaSuccess) s = MEGO_ECUDA;
+        if (s == MEGO_OK) s = mego_batch_resample(b, stream);
+        if (s == MEGO_OK && (cudaEventRecord(e1, st) != cudaSuccess ||
+                             cudaEventSynchronize(e1) != cudaSuccess ||
+                             cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+          s = MEGO_ECUDA;
+        total += ms;
+      }
+      if (s != MEGO_OK) {
+        status = s;
+        break;
+      }
+      if (total / reps < best) {
+        best = total / reps;
+        best_t = t;
+        best_p = p;
+      }
+    }
+    if (status != MEGO_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (status != MEGO_OK) return status;
+  const mego_status s = mego_batch_set_shape(b, best_t, best_p);
+  if (s == MEGO_OK && best_ms) *best_ms = best;
+  return s;
+}
+
+mego_status mego_batch_graph(mego_batch* b, double eps, int32_t b_max, void* stream) {
+  if (!b || !stream) return MEGO_EINVAL;  // capture needs a non-default stream
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (b->graph_exec) {
+    cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(b->graph_exec));
+    b->graph_exec = nullptr;
+  }
+  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return MEGO_ECUDA;
+  mego_status s = MEGO_OK;
+  if (eps > 0.0) s = mego_batch_bound(b, eps, b_max, stream);
+  if (s == MEGO_OK) s = mego_batch_resample(b, stream);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(st, &g);
+  if (s != MEGO_OK) {
+    if (g) cudaGraphDestroy(g);
+    return s;
+  }
+  if (e != cudaSuccess || !g) return MEGO_ECUDA;
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t ei = cudaGraphInstantiate(&exec, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) return MEGO_ECUDA;
+  b->graph_exec = exec;
+  return MEGO_OK;
+}
+
+mego_status mego_batch_launch_graph(const mego_batch* b, void* stream) {
+  if (!b || !b->graph_exec) return MEGO_EINVAL;
+  if (cudaGraphLaunch(static_cast<cudaGraphExec_t>(b->graph_exec),
+                      static_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return MEGO_ECUDA;
+  return MEGO_OK;
+}
+
+mego_status mego_batch_destroy(mego_batch* b) {
+  if (!b) return MEGO_EINVAL;
+  if (b->graph_exec) cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(b->graph_exec));
+  b->graph_exec = nullptr;
+  return MEGO_OK;
+}
+
+}  // extern "C"

@@ -139,24 +139,33 @@ mego_status choose_shape(int variant, uint32_t n, int gather, const mego_launch_
   return MEGO_OK;
 }
 
-// Round keys of Philox4x32-10 for a seed, and the constants of the stream
-// word (c2 = stream id) used by the hoisted generator.
-mego::PhiloxKeys make_keys(uint64_t seed, uint32_t sid) {
-  mego::PhiloxKeys K;
+}  // namespace
+
+namespace mego {
+
+// Round keys of Philox4x32-10 for a seed.
+RoundKeys make_round_keys(uint64_t seed) {
+  RoundKeys K;
   uint32_t k0 = static_cast<uint32_t>(seed & 0xFFFFFFFFull);
   uint32_t k1 = static_cast<uint32_t>(seed >> 32);
   for (int r = 0; r < 10; ++r) {
     K.rk0[r] = k0;
     K.rk1[r] = k1;
-    k0 += mego::kPhiloxW0;
-    k1 += mego::kPhiloxW1;
+    k0 += kPhiloxW0;
+    k1 += kPhiloxW1;
   }
-  const uint64_t m = static_cast<uint64_t>(mego::kPhiloxM1) * sid;
-  K.H = static_cast<uint32_t>(m >> 32) ^ K.rk0[0];
-  K.L = static_cast<uint32_t>(m);
-  K.sid = sid;
   return K;
 }
+
+// Constants of the stream word (c2 = stream id) used by the hoisted generator.
+StreamKey make_stream_key(const RoundKeys& K, uint32_t sid) {
+  const uint64_t m = static_cast<uint64_t>(kPhiloxM1) * sid;
+  return StreamKey{static_cast<uint32_t>(m >> 32) ^ K.rk0[0], static_cast<uint32_t>(m), sid};
+}
+
+}  // namespace mego
+
+namespace {
 
 // ---------------------------------------------------------------------------
 // Autotuning cache: best launch shape per (device, variant, gather layout,
@@ -306,20 +315,21 @@ mego_status mego_resample_gather(const float* d_w, int32_t n, int32_t B, const i
 
   mego::ResampleArgs a;
   std::memset(&a, 0, sizeof a);
-  a.w = d_w;
+  a.p.w = d_w;
+  a.p.anc = d_anc;
+  a.p.x_in = d_x_in;
+  a.p.x_out = d_x_out;
+  a.p.fault = nullptr;
+  a.p.ld = ld;
+  a.p.n = un;
+  a.p.nseg = (un + 31u) / 32u;
+  a.p.dim = dim;
+  a.p.nw = nw;
+  a.p.npart = npart;
+  a.K = mego::make_round_keys(seed);
+  a.p.S = mego::make_stream_key(a.K, stream_id);
   a.B_dev = d_B;
-  a.anc = d_anc;
-  a.x_in = d_x_in;
-  a.x_out = d_x_out;
-  a.fault = nullptr;
-  a.ld = ld;
-  a.n = un;
-  a.nseg = (un + 31u) / 32u;
   a.B = d_B ? 0 : B;
-  a.K = make_keys(seed, stream_id);
-  a.dim = dim;
-  a.nw = nw;
-  a.npart = npart;
   const cudaError_t e =
       launch_variant(variant, shape, gather, a, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return MEGO_ECUDA;

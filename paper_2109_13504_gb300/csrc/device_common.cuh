@@ -17,13 +17,18 @@ constexpr uint32_t kTagCDraw = 5u;   // C1/C2 (j in partition, u) pairs
 constexpr uint32_t kPhiloxM0 = 0xD2511F53u, kPhiloxM1 = 0xCD9E8D57u;
 constexpr uint32_t kPhiloxW0 = 0x9E3779B9u, kPhiloxW1 = 0xBB67AE85u;
 
-// Round keys and stream constants of one launch, computed on the host:
-// rk0[r] = k0 + r W0, rk1[r] = k1 + r W1 (the key of round r), and for the
-// stream word c2 = sid: H = hi(M1 sid) ^ rk0[0], L = lo(M1 sid).  Passed in
-// the kernel parameters, so every round reads its key from the constant bank.
-struct PhiloxKeys {
+// Round keys of one launch (one seed), computed on the host: rk0[r] = k0 +
+// r W0, rk1[r] = k1 + r W1, the key of round r.  Passed in the kernel
+// parameters, so every round reads its key from the constant bank.
+struct RoundKeys {
   uint32_t rk0[10];
   uint32_t rk1[10];
+};
+
+// Constants of one random stream (counter word c2 = sid) under a seed:
+// H = hi(M1 sid) ^ rk0[0], L = lo(M1 sid), the parts of round 0 that do not
+// depend on the particle or the iteration.
+struct StreamKey {
   uint32_t H, L;
   uint32_t sid;
 };
@@ -49,7 +54,7 @@ __device__ __forceinline__ void philox_round(uint32_t& c0, uint32_t& c1, uint32_
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds, round r
 // keyed by (k0 + r W0, k1 + r W1).
 __device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2,
-                                               uint32_t c3, const PhiloxKeys& K) {
+                                               uint32_t c3, const RoundKeys& K) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) philox_round(c0, c1, c2, c3, K.rk0[r], K.rk1[r]);
   return make_uint4(c0, c1, c2, c3);
@@ -67,12 +72,13 @@ struct PhiloxLane {
   uint32_t h3;    // hi(M0 * c0) in round 2
   uint32_t l3;    // lo(M0 * c0) in round 2 (= c3 after round 2)
 
-  __device__ __forceinline__ void init(uint32_t i, uint32_t tag, const PhiloxKeys& K) {
+  __device__ __forceinline__ void init(uint32_t i, uint32_t tag, const RoundKeys& K,
+                                       const StreamKey& S) {
     const uint64_t p0 = mulwide(kPhiloxM0, i);
     const uint32_t c2_1 = hi32(p0) ^ tag ^ K.rk1[0];
     x1 = lo32(p0) ^ K.rk1[1];
     const uint64_t p1 = mulwide(kPhiloxM1, c2_1);
-    const uint32_t c0_2 = hi32(p1) ^ K.L ^ K.rk0[1];
+    const uint32_t c0_2 = hi32(p1) ^ S.L ^ K.rk0[1];
     c1_2 = lo32(p1);
     const uint64_t p2 = mulwide(kPhiloxM0, c0_2);
     h3 = hi32(p2);
@@ -80,14 +86,14 @@ struct PhiloxLane {
   }
 
   // Shared per g: round-1 c0 product of c0_1 = H ^ g.
-  static __device__ __forceinline__ void group(uint32_t g, const PhiloxKeys& K,
+  static __device__ __forceinline__ void group(uint32_t g, const StreamKey& S,
                                                uint32_t& mh, uint32_t& ml) {
-    const uint64_t m = mulwide(kPhiloxM0, K.H ^ g);
+    const uint64_t m = mulwide(kPhiloxM0, S.H ^ g);
     mh = hi32(m);
     ml = lo32(m);
   }
 
-  __device__ __forceinline__ uint4 gen(uint32_t mh, uint32_t ml, const PhiloxKeys& K) const {
+  __device__ __forceinline__ uint4 gen(uint32_t mh, uint32_t ml, const RoundKeys& K) const {
     // after round 1: (c0_2, c1_2, mh ^ x1, ml); round 2 needs c2_2 = mh ^ x1.
     const uint64_t p = mulwide(kPhiloxM1, mh ^ x1);
     uint32_t c0 = hi32(p) ^ c1_2 ^ K.rk0[2];
@@ -122,10 +128,16 @@ __device__ __forceinline__ uint32_t index32(uint32_t x, uint32_t n) {
 }
 
 // Megopolis offset o^(b) ~ U{0, n-1}: Philox counter (b, 0, sid, 1).
-__device__ __forceinline__ uint32_t mego_offset(const PhiloxKeys& K, uint32_t b,
-                                                uint32_t n) {
-  const uint4 x = philox4x32_10(b, 0u, K.sid, kTagOffset, K);
+__device__ __forceinline__ uint32_t mego_offset(const RoundKeys& K, const StreamKey& S,
+                                                uint32_t b, uint32_t n) {
+  const uint4 x = philox4x32_10(b, 0u, S.sid, kTagOffset, K);
   return index64(x.x, x.y, n);
+}
+
+// Stream constants for stream id sid (device side).
+__device__ __forceinline__ StreamKey stream_key(const RoundKeys& K, uint32_t sid) {
+  const uint64_t m = mulwide(kPhiloxM1, sid);
+  return StreamKey{hi32(m) ^ K.rk0[0], lo32(m), sid};
 }
 
 __device__ __forceinline__ uint32_t word_of(const uint4& x, int q) {

@@ -21,9 +21,9 @@ namespace mego {
 enum Variant : int { kMegopolis = 0, kMetropolis = 1, kC1 = 2, kC2 = 3 };
 enum Gather : int { kGatherNone = 0, kGatherSoa = 1, kGatherAos4 = 2 };
 
-struct ResampleArgs {
+// One resampling problem (one weight vector and its outputs).
+struct Problem {
   const float* w;
-  const int32_t* B_dev;  // non-null: read B here (device-side bound)
   int32_t* anc;          // [n] ancestors, may be null
   const float* x_in;     // gather source, may be null
   float* x_out;
@@ -31,11 +31,18 @@ struct ResampleArgs {
   int64_t ld;
   uint32_t n;
   uint32_t nseg;         // ceil(n / 32)
-  int32_t B;
   int32_t dim;
   uint32_t nw;           // C1/C2: weights per partition
   uint32_t npart;        // C1/C2: number of partitions
-  PhiloxKeys K;          // round keys for (seed, stream id)
+  StreamKey S;           // stream constants for (seed, stream id)
+};
+
+// Kernel parameters of a single resample.
+struct ResampleArgs {
+  Problem p;
+  const int32_t* B_dev;  // non-null: read B here (device-side bound)
+  int32_t B;
+  RoundKeys K;           // round keys of the seed
 };
 
 // Per-warp table of the 32 iterations of the current offset window:
@@ -58,7 +65,7 @@ __device__ __forceinline__ float ldw(const float* __restrict__ w, uint32_t j) {
 
 // Stage w[0, n) into dynamic shared memory.  Returns false (uniformly for the
 // CTA) if the bulk copy did not complete within the poll budget.
-__device__ __forceinline__ bool stage_weights(const ResampleArgs& a) {
+__device__ __forceinline__ bool stage_weights(const Problem& a) {
   __shared__ __align__(8) uint64_t bar;
   float* s_w = reinterpret_cast<float*>(g_dyn_smem);
   const uint32_t bytes = a.n * 4u;
@@ -91,7 +98,7 @@ __device__ __forceinline__ bool stage_weights(const ResampleArgs& a) {
 
 // Ancestor output and gather for the P particles of one batch.
 template <int P, int GATHER>
-__device__ __forceinline__ void finish_batch(const ResampleArgs& a, uint32_t ibase,
+__device__ __forceinline__ void finish_batch(const Problem& a, uint32_t ibase,
                                              const uint32_t (&k)[P],
                                              const bool (&live)[P]) {
 #pragma unroll
@@ -124,7 +131,7 @@ __device__ __forceinline__ void finish_batch(const ResampleArgs& a, uint32_t iba
 // Loads of one Megopolis iteration for the P segments of a batch when the
 // partitions may run past n: each index is reduced modulo n.
 template <int P, bool SMEM>
-__device__ __forceinline__ void mego_wrapped_loads(const ResampleArgs& a, int2 e,
+__device__ __forceinline__ void mego_wrapped_loads(const Problem& a, int2 e,
                                                    uint32_t lane, float (&wj)[P]) {
   const uint32_t n = a.n;
   const uint32_t x0 = static_cast<uint32_t>(e.x) + ((lane + static_cast<uint32_t>(e.y)) & 31u);
@@ -148,7 +155,7 @@ __device__ __forceinline__ void mego_wrapped_loads(const ResampleArgs& a, int2 e
 // iteration b of their last acceptance (a uniform value) and the ancestor
 // index is rebuilt from o^(b) once, after the last iteration.
 template <int P, bool SMEM, int GATHER>
-__device__ __forceinline__ void megopolis_batch(const ResampleArgs& a, int B,
+__device__ __forceinline__ void megopolis_batch(const Problem& a, const RoundKeys& K, int B,
                                                 uint32_t s0, uint32_t seg_hi,
                                                 uint32_t lane, int2* win) {
   const uint32_t n = a.n;
@@ -163,12 +170,12 @@ __device__ __forceinline__ void megopolis_batch(const ResampleArgs& a, int B,
     live[p] = (s0 + p < seg_hi) && (i < n);
     wk[p] = ldw<SMEM>(a.w, i < n ? i : n - 1u);
     kb[p] = -1;
-    ph[p].init(i, kTagMegoU, a.K);
+    ph[p].init(i, kTagMegoU, K, a.S);
   }
   uint32_t fast_mask = 0u;
   for (int b0 = 0; b0 < B; b0 += 4) {
     if ((b0 & 31) == 0) {
-      const uint32_t o = mego_offset(a.K, static_cast<uint32_t>(b0) + lane, n);
+      const uint32_t o = mego_offset(K, a.S, static_cast<uint32_t>(b0) + lane, n);
       uint32_t base = s0 * 32u + (o & ~31u);
       base = base >= n ? base - n : base;
       fast_mask = __ballot_sync(0xFFFFFFFFu, base + 32u * P <= n);
@@ -178,7 +185,7 @@ __device__ __forceinline__ void megopolis_batch(const ResampleArgs& a, int B,
     }
     const int t0 = b0 & 31;
     uint32_t mh, ml;
-    PhiloxLane::group(static_cast<uint32_t>(b0) >> 2, a.K, mh, ml);
+    PhiloxLane::group(static_cast<uint32_t>(b0) >> 2, a.S, mh, ml);
     float wj[4][P];
     if (B - b0 >= 4) {
       // Four full iterations.
@@ -197,7 +204,7 @@ __device__ __forceinline__ void megopolis_batch(const ResampleArgs& a, int B,
       }
       uint4 r[P];
 #pragma unroll
-      for (int p = 0; p < P; ++p) r[p] = ph[p].gen(mh, ml, a.K);
+      for (int p = 0; p < P; ++p) r[p] = ph[p].gen(mh, ml, K);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
 #pragma unroll
@@ -215,7 +222,7 @@ __device__ __forceinline__ void megopolis_batch(const ResampleArgs& a, int B,
         if (q < nb) mego_wrapped_loads<P, SMEM>(a, win[t0 + q], lane, wj[q]);
       uint4 r[P];
 #pragma unroll
-      for (int p = 0; p < P; ++p) r[p] = ph[p].gen(mh, ml, a.K);
+      for (int p = 0; p < P; ++p) r[p] = ph[p].gen(mh, ml, K);
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
         if (q < nb) {
@@ -234,7 +241,7 @@ __device__ __forceinline__ void megopolis_batch(const ResampleArgs& a, int B,
   for (int p = 0; p < P; ++p) {
     k[p] = ibase + 32u * p;
     if (kb[p] >= 0) {
-      const uint32_t o = mego_offset(a.K, static_cast<uint32_t>(kb[p]), n);
+      const uint32_t o = mego_offset(K, a.S, static_cast<uint32_t>(kb[p]), n);
       uint32_t x = (s0 + p) * 32u + (o & ~31u) + ((lane + o) & 31u);
       if (x >= n) x -= n;
       if (x >= n) x %= n;
@@ -248,7 +255,7 @@ __device__ __forceinline__ void megopolis_batch(const ResampleArgs& a, int B,
 // Metropolis (Algorithm 2): independent j ~ U{0, n-1} per particle and
 // iteration; two iterations per Philox call.
 template <int P, bool SMEM, int GATHER>
-__device__ __forceinline__ void metropolis_batch(const ResampleArgs& a, int B,
+__device__ __forceinline__ void metropolis_batch(const Problem& a, const RoundKeys& K, int B,
                                                  uint32_t s0, uint32_t seg_hi,
                                                  uint32_t lane) {
   const uint32_t n = a.n;
@@ -263,15 +270,15 @@ __device__ __forceinline__ void metropolis_batch(const ResampleArgs& a, int B,
     live[p] = (s0 + p < seg_hi) && (i < n);
     k[p] = i < n ? i : n - 1u;
     wk[p] = ldw<SMEM>(a.w, k[p]);
-    ph[p].init(i, kTagMetro, a.K);
+    ph[p].init(i, kTagMetro, K, a.S);
   }
   for (int b0 = 0; b0 < B; b0 += 2) {
     const int nb = (B - b0) < 2 ? (B - b0) : 2;
     uint32_t mh, ml;
-    PhiloxLane::group(static_cast<uint32_t>(b0) >> 1, a.K, mh, ml);
+    PhiloxLane::group(static_cast<uint32_t>(b0) >> 1, a.S, mh, ml);
     uint4 r[P];
 #pragma unroll
-    for (int p = 0; p < P; ++p) r[p] = ph[p].gen(mh, ml, a.K);
+    for (int p = 0; p < P; ++p) r[p] = ph[p].gen(mh, ml, K);
     float wj[2][P];
     uint32_t jj[2][P];
 #pragma unroll
@@ -303,7 +310,7 @@ __device__ __forceinline__ void metropolis_batch(const ResampleArgs& a, int B,
 // Metropolis-C1 / C2 (Algorithms 3, 4): j uniform inside partition p of nw
 // weights; p drawn per 32-particle segment once (C1) or per iteration (C2).
 template <int VARIANT, int P, bool SMEM, int GATHER>
-__device__ __forceinline__ void partition_batch(const ResampleArgs& a, int B,
+__device__ __forceinline__ void partition_batch(const Problem& a, const RoundKeys& K, int B,
                                                 uint32_t s0, uint32_t seg_hi,
                                                 uint32_t lane) {
   const uint32_t n = a.n;
@@ -319,10 +326,10 @@ __device__ __forceinline__ void partition_batch(const ResampleArgs& a, int B,
     live[p] = (s0 + p < seg_hi) && (i < n);
     k[p] = i < n ? i : n - 1u;
     wk[p] = ldw<SMEM>(a.w, k[p]);
-    ph[p].init(i, kTagCDraw, a.K);
+    ph[p].init(i, kTagCDraw, K, a.S);
     part[p] = 0u;
     if constexpr (VARIANT == kC1) {
-      const uint4 x = philox4x32_10(s0 + p, 0u, a.K.sid, kTagCPart, a.K);
+      const uint4 x = philox4x32_10(s0 + p, 0u, a.S.sid, kTagCPart, K);
       part[p] = index64(x.x, x.y, a.npart);
     }
   }
@@ -335,15 +342,15 @@ __device__ __forceinline__ void partition_batch(const ResampleArgs& a, int B,
     if constexpr (VARIANT == kC2) {
       if ((b0 % kStepsPerFill) == 0) {
         const uint32_t bb = static_cast<uint32_t>(b0) + lane / P;
-        const uint4 x = philox4x32_10(s0 + lane % P, bb + 1u, a.K.sid, kTagCPart, a.K);
+        const uint4 x = philox4x32_10(s0 + lane % P, bb + 1u, a.S.sid, kTagCPart, K);
         part_reg = index64(x.x, x.y, a.npart);
       }
     }
     uint32_t mh, ml;
-    PhiloxLane::group(static_cast<uint32_t>(b0) >> 1, a.K, mh, ml);
+    PhiloxLane::group(static_cast<uint32_t>(b0) >> 1, a.S, mh, ml);
     uint4 r[P];
 #pragma unroll
-    for (int p = 0; p < P; ++p) r[p] = ph[p].gen(mh, ml, a.K);
+    for (int p = 0; p < P; ++p) r[p] = ph[p].gen(mh, ml, K);
     float wj[2][P];
     uint32_t jj[2][P];
 #pragma unroll
@@ -377,32 +384,41 @@ __device__ __forceinline__ void partition_batch(const ResampleArgs& a, int B,
 }
 
 // ---------------------------------------------------------------------------
+// The chains of whole batches [seg_lo, seg_hi) of one problem for one warp.
+template <int VARIANT, int P, bool SMEM, int GATHER>
+__device__ __forceinline__ void run_segments(const Problem& a, const RoundKeys& K, int B,
+                                             uint32_t seg_lo, uint32_t seg_hi, uint32_t lane,
+                                             int2* win) {
+  for (uint32_t s0 = seg_lo; s0 < seg_hi; s0 += P) {
+    if constexpr (VARIANT == kMegopolis) {
+      megopolis_batch<P, SMEM, GATHER>(a, K, B, s0, seg_hi, lane, win);
+    } else if constexpr (VARIANT == kMetropolis) {
+      metropolis_batch<P, SMEM, GATHER>(a, K, B, s0, seg_hi, lane);
+    } else {
+      partition_batch<VARIANT, P, SMEM, GATHER>(a, K, B, s0, seg_hi, lane);
+    }
+  }
+}
+
 template <int VARIANT, int P, bool SMEM, int GATHER>
 __global__ void __launch_bounds__(256) resample_kernel(const __grid_constant__ ResampleArgs a) {
   __shared__ int2 s_win[kMaxWarps][32];
   const int B = a.B_dev ? *a.B_dev : a.B;
   if (B < 0) return;  // device-side bound failed: write nothing
   if constexpr (SMEM) {
-    if (!stage_weights(a)) return;
+    if (!stage_weights(a.p)) return;
   }
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t wpb = blockDim.x >> 5;
   const uint64_t gw = static_cast<uint64_t>(blockIdx.x) * wpb + (threadIdx.x >> 5);
   const uint64_t tw = static_cast<uint64_t>(gridDim.x) * wpb;
   // Whole batches of P segments per warp, in equal contiguous ranges.
-  const uint64_t nbat = (a.nseg + P - 1u) / P;
+  const uint64_t nbat = (a.p.nseg + P - 1u) / P;
   const uint32_t seg_lo = static_cast<uint32_t>(nbat * gw / tw) * P;
   uint32_t seg_hi = static_cast<uint32_t>(nbat * (gw + 1u) / tw) * P;
-  if (seg_hi > a.nseg) seg_hi = a.nseg;
-  for (uint32_t s0 = seg_lo; s0 < seg_hi; s0 += P) {
-    if constexpr (VARIANT == kMegopolis) {
-      megopolis_batch<P, SMEM, GATHER>(a, B, s0, seg_hi, lane, s_win[threadIdx.x >> 5]);
-    } else if constexpr (VARIANT == kMetropolis) {
-      metropolis_batch<P, SMEM, GATHER>(a, B, s0, seg_hi, lane);
-    } else {
-      partition_batch<VARIANT, P, SMEM, GATHER>(a, B, s0, seg_hi, lane);
-    }
-  }
+  if (seg_hi > a.p.nseg) seg_hi = a.p.nseg;
+  run_segments<VARIANT, P, SMEM, GATHER>(a.p, a.K, B, seg_lo, seg_hi, lane,
+                                         s_win[threadIdx.x >> 5]);
 }
 
 // Host-side launcher for one variant (defined in resample_<variant>.cu).
@@ -413,6 +429,10 @@ struct LaunchShape {
   int grid;
   size_t smem_bytes;
 };
+
+// Host helpers (capi.cu): round keys of a seed, constants of a stream.
+RoundKeys make_round_keys(uint64_t seed);
+StreamKey make_stream_key(const RoundKeys& K, uint32_t sid);
 
 // Opt a kernel in to the largest dynamic shared-memory size it can use
 // (the per-block opt-in limit minus its static shared memory), once per

@@ -1,0 +1,135 @@
+"""Batched resampling (many filters, one persistent launch) against single
+resamples and the oracle.  Each filter's ancestors must equal, bit for bit,
+those of mego_resample_gather with the same seed, stream id and B -- alone or
+in the batch -- and the per-filter bound must equal the oracle's (near-integer
+rule as in test_gpu_parity)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synthetic
+
+pytestmark = pytest.mark.gpu
+
+mego = pytest.importorskip("paper_2109_13504_gb300")
+DEV = torch.device("cuda:0")
+SEED = 77
+
+
+def _b_equal(B_gpu, B_cpu, q):
+    return B_gpu == B_cpu or (abs(q - round(q)) <= 1e-9 * max(1.0, abs(q))
+                              and abs(B_gpu - B_cpu) <= 1)
+
+
+def _make(count, seed, lo=5.0, hi=14.0, sizes=None):
+    ns, ys = synthetic.filter_sizes(count, lo, hi, seed)
+    if sizes is not None:
+        ns = np.array(sizes, dtype=np.int64)
+        ys = ys[: len(ns)]
+    ws = [synthetic.gaussian_weights(int(n), float(y), 1000 + f) for f, (n, y) in enumerate(zip(ns, ys))]
+    return ws
+
+
+@pytest.mark.parametrize("variant", [mego.MEGOPOLIS, mego.METROPOLIS])
+def test_batch_matches_single_resamples_and_oracle(variant):
+    ws = _make(40, 3, sizes=[1, 2, 31, 32, 33, 100, 127, 128, 129, 4097] + [0] * 0) + _make(30, 4)
+    filters = []
+    for f, w_h in enumerate(ws):
+        w = torch.from_numpy(w_h).to(DEV)
+        fixed = (f % 3 == 0)
+        filters.append({"w": w, "anc": torch.full((w_h.size,), -3, dtype=torch.int32, device=DEV),
+                        "B": (f % 17) if fixed else -1, "stream_id": 500 + f})
+    batch = mego.Batch(filters, variant=variant, seed=SEED)
+    batch.bound(0.01)
+    batch.resample()
+    torch.cuda.synchronize()
+    Bb = batch.B.cpu().numpy()
+    st = batch.status.cpu().numpy()
+    q = batch.q.cpu().numpy()
+    for f, (d, w_h) in enumerate(zip(filters, ws)):
+        assert st[f] == mego.MEGO_OK
+        s_ref, B_ref, q_ref = oracle.compute_B(w_h, 0.01)
+        assert _b_equal(int(Bb[f]), B_ref, q_ref), (f, Bb[f], B_ref)
+        B = d["B"] if d["B"] >= 0 else int(Bb[f])
+        got = d["anc"].cpu().numpy()
+        alone = mego.mego_resample_gather(d["w"], B, None, SEED, d["stream_id"], variant,
+                                          anc=torch.empty_like(d["anc"]))[0].cpu().numpy()
+        assert np.array_equal(got, alone), f
+        if w_h.size <= 5000:
+            assert np.array_equal(got, oracle.resample(w_h, B, SEED, variant,
+                                                       stream_id=d["stream_id"])), f
+
+
+def test_batch_graph_replay_and_shapes_and_autotune():
+    ws = _make(64, 9, 6.0, 13.0)
+    filters = [{"w": torch.from_numpy(w_h).to(DEV),
+                "anc": torch.empty(w_h.size, dtype=torch.int32, device=DEV),
+                "B": -1, "stream_id": f} for f, w_h in enumerate(ws)]
+    batch = mego.Batch(filters, seed=5)
+    batch.bound(0.01)
+    batch.resample()
+    torch.cuda.synchronize()
+    ref = [d["anc"].clone() for d in filters]
+    for threads, ppt in [(64, 1), (128, 2), (256, 4)]:
+        batch.set_shape(threads, ppt)
+        for d in filters:
+            d["anc"].fill_(-1)
+        batch.resample()
+        torch.cuda.synchronize()
+        assert all(torch.equal(a, d["anc"]) for a, d in zip(ref, filters))
+    ms = batch.autotune(reps=2)
+    assert ms > 0 and batch.shape["threads"] in (64, 128, 256)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        batch.capture(0.01, stream=side)
+        for _ in range(3):                 # the work queue resets itself between launches
+            for d in filters:
+                d["anc"].fill_(-1)
+            batch.replay(stream=side)
+            side.synchronize()
+            assert all(torch.equal(a, d["anc"]) for a, d in zip(ref, filters))
+    batch.close()
+
+
+@pytest.mark.parametrize("layout", [mego.LAYOUT_SOA, mego.LAYOUT_AOS4])
+def test_batch_gather(layout):
+    ws = _make(12, 11, 7.0, 12.0)
+    filters = []
+    for f, w_h in enumerate(ws):
+        n = w_h.size
+        if layout == mego.LAYOUT_SOA:
+            x = torch.from_numpy(synthetic.gaussian_state(n, 3, f)).to(DEV)
+        else:
+            x = torch.from_numpy(np.ascontiguousarray(synthetic.gaussian_state(n, 4, f).T)).to(DEV)
+        filters.append({"w": torch.from_numpy(w_h).to(DEV), "x_in": x,
+                        "x_out": torch.empty_like(x),
+                        "anc": torch.empty(n, dtype=torch.int32, device=DEV),
+                        "B": 20 + f, "stream_id": 7 * f})
+    batch = mego.Batch(filters, layout=layout, seed=SEED)
+    batch.resample()
+    torch.cuda.synchronize()
+    for f, d in enumerate(filters):
+        ref = oracle.resample(ws[f], d["B"], SEED, mego.MEGOPOLIS, stream_id=d["stream_id"])
+        assert np.array_equal(d["anc"].cpu().numpy(), ref)
+        xi = d["x_in"].cpu().numpy()
+        want = oracle.gather_soa(xi, ref) if layout == mego.LAYOUT_SOA else oracle.gather_aos4(xi, ref)
+        assert np.array_equal(d["x_out"].cpu().numpy(), want)
+
+
+def test_batch_bad_filter_is_isolated():
+    ws = _make(6, 2, 8.0, 10.0)
+    ws[2] = ws[2].copy()
+    ws[2][5] = np.nan
+    filters = [{"w": torch.from_numpy(w_h).to(DEV),
+                "anc": torch.full((w_h.size,), -9, dtype=torch.int32, device=DEV),
+                "B": -1, "stream_id": f} for f, w_h in enumerate(ws)]
+    batch = mego.Batch(filters, seed=1)
+    batch.bound(0.01)
+    batch.resample()
+    torch.cuda.synchronize()
+    st = batch.status.cpu().numpy()
+    assert st[2] == mego.MEGO_EWEIGHTS and int(batch.B[2].item()) == -1
+    assert (filters[2]["anc"].cpu().numpy() == -9).all()
+    for f in (0, 1, 3, 4, 5):
+        assert st[f] == mego.MEGO_OK and (filters[f]["anc"].cpu().numpy() >= 0).all()
