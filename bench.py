@@ -247,6 +247,56 @@ def _batched_leg(args, mego, synthetic, torch, dev):
             "shape": shape}
 
 
+def _serving_leg(args, mego, synthetic, torch, dev):
+    """Poisson arrivals (20k req/s), N = floor(2^U[10,20]), y = 2 weights and
+    a 4-dim AoS state per request, 40 GB device budget: the continuous-
+    batching server against the same server taking one request per launch
+    on one stream (unbatched sequential calls).  Latency runs from a
+    request's submission to its ancestors and gathered state being in host
+    memory."""
+    import numpy as np
+    count = args.serve_requests
+    t_arr, sizes = synthetic.request_stream(count, 20000.0, 10.0, 20.0, 5)
+    pool = 8
+    nmax = 1 << 20
+    w_pool = [torch.from_numpy(synthetic.gaussian_weights(nmax, 2.0, 900 + k)).pin_memory()
+              for k in range(pool)]
+    x_pool = [torch.from_numpy(np.ascontiguousarray(
+        synthetic.gaussian_state(nmax, 4, 950 + k).T)).pin_memory() for k in range(pool)]
+    a_pool = [torch.empty(nmax, dtype=torch.int32).pin_memory() for _ in range(pool)]
+    o_pool = [torch.empty((nmax, 4), dtype=torch.float32).pin_memory() for _ in range(pool)]
+    reqs = [(k, w_pool[k % pool][:int(n)], x_pool[k % pool][:int(n)],
+             a_pool[k % pool][:int(n)], o_pool[k % pool][:int(n)])
+            for k, n in enumerate(sizes)]
+    total = int(sum(int(n) for n in sizes))
+    budget = min(40 << 30, int(torch.cuda.mem_get_info(dev)[0] * 0.5))
+    out = {"workload": "%d requests, Poisson 20k req/s, N=floor(2^U[10,20]) (sum %d), "
+                       "y=2 weights, 4-dim AoS4 state gather, Megopolis, B from Eq. 3 "
+                       "(eps=0.01) per request" % (count, total),
+           "budget_bytes": budget}
+    for name, mb, ns in (("continuous_batching", 256, 2), ("unbatched_sequential", 1, 1)):
+        server = mego.Server(arena_bytes=budget, seed=SEED, max_batch=mb, streams=ns,
+                             device=dev)
+        t0 = time.perf_counter()
+        server.replay(reqs, t_arr, timeout_s=300.0)
+        span = time.perf_counter() - t0
+        done = server.poll(count + 16)
+        st = server.stats()
+        server.close()
+        lat = sorted(c[3] / 1e6 for c in done)
+        ok = sum(1 for c in done if c[1] == mego.MEGO_OK)
+        out[name] = {"completed": ok, "makespan_s": span,
+                     "throughput_particles_per_s": total / span,
+                     "throughput_requests_per_s": count / span,
+                     "latency_ms_p50": lat[len(lat) // 2],
+                     "latency_ms_p99": lat[min(len(lat) - 1, int(0.99 * (len(lat) - 1)))],
+                     "batches": st["batches"], "max_batch": st["max_batch"],
+                     "peak_device_bytes": st["peak_arena_bytes"]}
+        del server
+    out["arrival_span_s"] = float(t_arr[-1])
+    return out
+
+
 def run_reference(args):
     """The reference arm: the CPU oracle as it stands, timed on the host."""
     world, rank, _ = _dist()
@@ -454,6 +504,7 @@ def run_gpu(args):
     e2e_value = N * len(YS) * e2e_steps / e2e_s
 
     batched = _batched_leg(args, mego, synthetic, torch, dev)
+    serving = _serving_leg(args, mego, synthetic, torch, dev) if args.serve_requests > 0 else None
 
     if rank != 0:
         if dist is not None:
@@ -517,6 +568,7 @@ def run_gpu(args):
                                      "l2_probe_gbs": l2_best,
                                      "frac_of_l2_probe": achieved_gbs / l2_best}},
         "batched": batched,
+        "serving": serving,
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": 4 * N * len(YS),
@@ -580,6 +632,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=1 << 20)
     ap.add_argument("--reference-sample", type=int, default=1 << 12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=2000,
+                    help="requests in the serving leg (0 skips it)")
     ap.add_argument("--case", choices=sorted(PROFILE_CASES),
                     help="run one kernel case (for profilers) instead of the benchmark")
     args = ap.parse_args()

@@ -270,6 +270,72 @@ mego_status mego_batch_launch_graph(const mego_batch* b, void* stream);
 mego_status mego_batch_destroy(mego_batch* b);
 
 /* ----------------------------------------------------------------------
+ * Serving: a continuous-batching request loop (a library service; the paper
+ * has no serving system).  One worker thread admits queued requests in FIFO
+ * order while their device buffers (40 n bytes each: weights, ancestors, and
+ * AoS4 state in and out) fit in the caller's arena -- the device-memory
+ * budget -- and sends every admitted request through one batched launch
+ * (bound + Megopolis/Metropolis + gather) on a free stream of its own, with
+ * the uploads and the copies of the results to the request's host buffers
+ * on the same stream.  Requests arriving while batches run join the next
+ * batch, so work from different arrivals overlaps on the GPU.  A request is
+ * resampled with the server's seed and stream id = (uint32) id, so its
+ * result equals mego_resample_gather with that seed and stream id (B from
+ * the bound) whatever it was batched with.  Host buffers of a request must
+ * stay valid until its completion is polled; page-locked buffers copy fastest.
+ */
+typedef struct mego_request {
+  uint64_t id;          /* request id; its low 32 bits are the stream id      */
+  const float* h_w;     /* [n] weights (host)                                 */
+  const float* h_x;     /* [n][4] state (host), or NULL if the server has none */
+  int32_t* h_anc;       /* [n] ancestors out (host), or NULL                  */
+  float* h_x_out;       /* [n][4] gathered state out (host), or NULL          */
+  int32_t n;
+} mego_request;
+
+typedef struct mego_completion {
+  uint64_t id;
+  int32_t status;       /* MEGO_OK, or the error that failed the batch        */
+  int32_t n;
+  int64_t latency_ns;   /* from submission to the results being on the host   */
+} mego_completion;
+
+typedef struct mego_server_cfg {
+  void* d_arena;        /* device memory budget (256-byte aligned, caller's)  */
+  size_t arena_bytes;
+  uint64_t seed;
+  double eps;           /* bound of Eq. 3 per request                          */
+  int32_t variant;      /* MEGO_MEGOPOLIS or MEGO_METROPOLIS                   */
+  int32_t max_batch;    /* requests per batch (0: 256)                        */
+  int32_t streams;      /* batches in flight (0: 2)                           */
+  int32_t threads, ppt; /* batch launch shape (0: default)                    */
+  int32_t poll_us;      /* worker poll interval while busy (0: 5 us)          */
+  int32_t with_state;   /* 1: every request carries AoS4 state; 0: none does  */
+} mego_server_cfg;
+
+typedef struct mego_server_stats_t {
+  uint64_t batches, max_batch, peak_arena_bytes, queued, inflight;
+} mego_server_stats_t;
+
+typedef struct mego_server mego_server;
+
+mego_status mego_server_create(const mego_server_cfg* cfg, mego_server** out);
+/* Queue a request (non-blocking).  MEGO_ENOMEM if it can never fit the
+ * arena; MEGO_EINVAL if its state does not match with_state. */
+mego_status mego_server_submit(mego_server* s, const mego_request* r);
+/* Move up to max_out completions to out; returns how many. */
+int32_t mego_server_poll(mego_server* s, mego_completion* out, int32_t max_out);
+/* Wait until nothing is queued or running (MEGO_ETIMEOUT after timeout_s). */
+mego_status mego_server_drain(mego_server* s, double timeout_s);
+mego_status mego_server_stats(mego_server* s, mego_server_stats_t* out);
+mego_status mego_server_destroy(mego_server* s);
+/* Submit reqs[k] at t_arrival[k] seconds after the call (open-loop arrival
+ * schedule, busy-waiting between arrivals), then drain. */
+mego_status mego_server_replay(mego_server* s, const mego_request* reqs,
+                               const double* t_arrival, int32_t count,
+                               double timeout_s);
+
+/* ----------------------------------------------------------------------
  * Wait for `stream` up to timeout_s seconds by polling an event, then copy
  * the device status word to *h_status.  Returns MEGO_ETIMEOUT (and leaves
  * *h_status untouched) if the stream has not drained by the deadline. */

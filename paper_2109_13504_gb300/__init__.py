@@ -74,6 +74,30 @@ class BatchHandle(ctypes.Structure):
                 ("cfg", LaunchCfg), ("grid", ctypes.c_int32), ("graph_exec", ctypes.c_void_p)]
 
 
+class Request(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("h_w", ctypes.c_void_p), ("h_x", ctypes.c_void_p),
+                ("h_anc", ctypes.c_void_p), ("h_x_out", ctypes.c_void_p), ("n", ctypes.c_int32)]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int32), ("n", ctypes.c_int32),
+                ("latency_ns", ctypes.c_int64)]
+
+
+class ServerCfg(ctypes.Structure):
+    _fields_ = [("d_arena", ctypes.c_void_p), ("arena_bytes", ctypes.c_size_t),
+                ("seed", ctypes.c_uint64), ("eps", ctypes.c_double), ("variant", ctypes.c_int32),
+                ("max_batch", ctypes.c_int32), ("streams", ctypes.c_int32),
+                ("threads", ctypes.c_int32), ("ppt", ctypes.c_int32), ("poll_us", ctypes.c_int32),
+                ("with_state", ctypes.c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("batches", ctypes.c_uint64), ("max_batch", ctypes.c_uint64),
+                ("peak_arena_bytes", ctypes.c_uint64), ("queued", ctypes.c_uint64),
+                ("inflight", ctypes.c_uint64)]
+
+
 _lib = None
 
 
@@ -117,6 +141,14 @@ def _load():
         "mego_batch_graph": ([ctypes.POINTER(BatchHandle), f64, i32, vp], ci),
         "mego_batch_launch_graph": ([ctypes.POINTER(BatchHandle), vp], ci),
         "mego_batch_destroy": ([ctypes.POINTER(BatchHandle)], ci),
+        "mego_server_create": ([ctypes.POINTER(ServerCfg), ctypes.POINTER(ctypes.c_void_p)], ci),
+        "mego_server_submit": ([vp, ctypes.POINTER(Request)], ci),
+        "mego_server_poll": ([vp, ctypes.POINTER(Completion), i32], i32),
+        "mego_server_drain": ([vp, f64], ci),
+        "mego_server_stats": ([vp, ctypes.POINTER(ServerStats)], ci),
+        "mego_server_destroy": ([vp], ci),
+        "mego_server_replay": ([vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_double),
+                                i32, f64], ci),
         "mego_autotune": ([vp, i32, i32, ci, u32, vp, vp, i32, ctypes.c_int64, ci, vp, i32,
                            ctypes.POINTER(LaunchCfg), ctypes.POINTER(ctypes.c_float), vp], ci),
     }
@@ -495,6 +527,85 @@ class Batch:
     def close(self):
         if getattr(self, "handle", None) is not None and _lib is not None:
             _lib.mego_batch_destroy(ctypes.byref(self.handle))
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# --------------------------------------------------------------------------
+# Serving
+
+
+def _host_ptr(t: Optional[torch.Tensor], dtype, name: str):
+    if t is None:
+        return None
+    if t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise TypeError("%s must be a contiguous host tensor of %s" % (name, dtype))
+    return t.data_ptr()
+
+
+class Server:
+    """Continuous-batching resample server over a device arena (the memory
+    budget).  Requests carry host tensors: w [n] float32, optionally x
+    [n, 4] float32 state, and outputs anc [n] int32 / x_out [n, 4]."""
+
+    def __init__(self, arena_bytes: int, seed: int = 0, eps: float = 0.01,
+                 variant: int = MEGOPOLIS, max_batch: int = 256, streams: int = 2,
+                 with_state: bool = True, threads: int = 0, ppt: int = 0, poll_us: int = 0,
+                 device=None):
+        lib = _load()
+        dev = device or torch.device("cuda", torch.cuda.current_device())
+        self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device=dev)
+        cfg = ServerCfg(self.arena.data_ptr(), int(arena_bytes), int(seed), float(eps),
+                        int(variant), int(max_batch), int(streams), int(threads), int(ppt),
+                        int(poll_us), 1 if with_state else 0)
+        self._h = ctypes.c_void_p()
+        _check(lib.mego_server_create(ctypes.byref(cfg), ctypes.byref(self._h)),
+               "mego_server_create")
+        self._keep = {}
+
+    def _req(self, rid, w, x=None, anc=None, x_out=None):
+        return Request(int(rid), _host_ptr(w, torch.float32, "w"),
+                       _host_ptr(x, torch.float32, "x"), _host_ptr(anc, torch.int32, "anc"),
+                       _host_ptr(x_out, torch.float32, "x_out"), int(w.numel()))
+
+    def submit(self, rid: int, w, x=None, anc=None, x_out=None):
+        r = self._req(rid, w, x, anc, x_out)
+        self._keep[int(rid)] = (w, x, anc, x_out)
+        _check(_load().mego_server_submit(self._h, ctypes.byref(r)), "mego_server_submit")
+
+    def poll(self, max_out: int = 4096):
+        buf = (Completion * max_out)()
+        k = _load().mego_server_poll(self._h, buf, int(max_out))
+        out = [(c.id, c.status, c.n, c.latency_ns) for c in buf[:k]]
+        for c in out:
+            self._keep.pop(int(c[0]), None)
+        return out
+
+    def drain(self, timeout_s: float = 60.0):
+        _check(_load().mego_server_drain(self._h, float(timeout_s)), "mego_server_drain")
+
+    def replay(self, requests, t_arrival, timeout_s: float = 120.0):
+        """requests: list of (id, w, x, anc, x_out) host tensors."""
+        arr = (Request * len(requests))(*[self._req(*r) for r in requests])
+        t = (ctypes.c_double * len(requests))(*[float(v) for v in t_arrival])
+        _check(_load().mego_server_replay(self._h, arr, t, len(requests), float(timeout_s)),
+               "mego_server_replay")
+
+    def stats(self):
+        st = ServerStats()
+        _check(_load().mego_server_stats(self._h, ctypes.byref(st)), "mego_server_stats")
+        return {"batches": st.batches, "max_batch": st.max_batch,
+                "peak_arena_bytes": st.peak_arena_bytes, "queued": st.queued,
+                "inflight": st.inflight}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _load().mego_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
 
     def __del__(self):
         try:
