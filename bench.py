@@ -297,6 +297,63 @@ def _serving_leg(args, mego, synthetic, torch, dev):
     return out
 
 
+def _sir_leg(args, mego, synthetic, torch, dev):
+    """End-to-end modified SIR filter (Algorithm 6, model of Eqs. 22-23),
+    N = 2^20, T = 100 steps, fixed B in {16, 32, 64}, Megopolis and
+    Metropolis: RMSE (Eq. 24) over trajectories x runs and the resample ratio
+    (Eq. 25) from CUDA-event times of the three stages."""
+    import math
+    import numpy as np
+    n, T = 1 << 20, 100
+    trajs, runs = args.sir_trajectories, args.sir_runs
+    stream = torch.cuda.current_stream(dev)
+    out = {"workload": "N=2^20, T=100, %d synthetic trajectories x %d runs, x_0=0.1, "
+                       "particles from N(0,2)" % (trajs, runs)}
+    truths = [synthetic.sir_truth(T, 500 + j) for j in range(trajs)]
+    for variant, vname in ((mego.MEGOPOLIS, "megopolis"), (mego.METROPOLIS, "metropolis")):
+        for B in (16, 32, 64):
+            tau = [0.0, 0.0, 0.0]
+            rmse = []
+            for j, (xt, zt) in enumerate(truths):
+                sq = []
+                for r in range(runs):
+                    x = torch.from_numpy(synthetic.sir_initial_particles(n, 600 + r)).to(dev)
+                    noise = synthetic.sir_process_noise(n, T, 700 + 31 * j + r, device=dev)
+                    xs = torch.empty((1, n), dtype=torch.float32, device=dev)
+                    xp = torch.empty(n, dtype=torch.float32, device=dev)
+                    w = torch.empty(n, dtype=torch.float32, device=dev)
+                    est = torch.empty(T + 1, dtype=torch.float64, device=dev)
+                    ws = torch.empty(int(mego._load().mego_mean_workspace_bytes()),
+                                     dtype=torch.uint8, device=dev)
+                    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)]
+                          for _ in range(T)]
+                    for t in range(1, T + 1):
+                        e = ev[t - 1]
+                        e[0].record(stream)
+                        mego.mego_sir_predict_update(x, noise[t - 1], 8 * math.cos(1.2 * t),
+                                                     float(zt[t]), x_pred=xp, w=w)
+                        e[1].record(stream)
+                        mego.mego_resample_gather(w, B, None, 1000 * j + r, t, variant,
+                                                  x_in=xp.view(1, n), x_out=xs)
+                        e[2].record(stream)
+                        mego.mego_mean(xs.view(-1), out=est[t:t + 1], ws=ws)
+                        e[3].record(stream)
+                        x, xs = xs.view(-1), x.view(1, n)
+                    torch.cuda.synchronize(dev)
+                    for e in ev:
+                        tau[0] += e[0].elapsed_time(e[1])
+                        tau[1] += e[1].elapsed_time(e[2])
+                        tau[2] += e[2].elapsed_time(e[3])
+                    sq.append((est.cpu().numpy()[1:] - xt[1:]) ** 2)
+                rmse.append(float(np.mean(np.sqrt(np.mean(sq, axis=0)))))
+            out["%s_B%d" % (vname, B)] = {
+                "rmse": float(np.mean(rmse)),
+                "resample_ratio": tau[1] / sum(tau),
+                "ms_per_step": sum(tau) / (T * trajs * runs),
+                "resample_ms_per_step": tau[1] / (T * trajs * runs)}
+    return out
+
+
 def run_reference(args):
     """The reference arm: the CPU oracle as it stands, timed on the host."""
     world, rank, _ = _dist()
@@ -505,6 +562,7 @@ def run_gpu(args):
 
     batched = _batched_leg(args, mego, synthetic, torch, dev)
     serving = _serving_leg(args, mego, synthetic, torch, dev) if args.serve_requests > 0 else None
+    sir = _sir_leg(args, mego, synthetic, torch, dev) if args.sir_trajectories > 0 else None
 
     if rank != 0:
         if dist is not None:
@@ -569,6 +627,7 @@ def run_gpu(args):
                                      "frac_of_l2_probe": achieved_gbs / l2_best}},
         "batched": batched,
         "serving": serving,
+        "sir_filter": sir,
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": 4 * N * len(YS),
@@ -634,6 +693,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests in the serving leg (0 skips it)")
+    ap.add_argument("--sir-trajectories", type=int, default=4,
+                    help="trajectories in the SIR filter leg (0 skips it)")
+    ap.add_argument("--sir-runs", type=int, default=4)
     ap.add_argument("--case", choices=sorted(PROFILE_CASES),
                     help="run one kernel case (for profilers) instead of the benchmark")
     args = ap.parse_args()

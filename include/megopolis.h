@@ -336,6 +336,26 @@ mego_status mego_server_replay(mego_server* s, const mego_request* reqs,
                                double timeout_s);
 
 /* ----------------------------------------------------------------------
+ * Stages of the modified SIR filter around the resampler (Algorithm 6,
+ * model of Eqs. 22-23).
+ * mego_sir_predict_update: for each particle i,
+ *   x_pred[i] = x[i]/2 + 25 x[i]/(1 + x[i]^2) + drift + v[i]
+ *   w[i]      = exp(-(z - x_pred[i]^2 / 20)^2 / 2)
+ * with drift = 8 cos(1.2 t) and v the process noise (both from the caller),
+ * z the measurement.  Binary32 operations in that order, no contraction;
+ * expf within 2 ulp.  d_x, d_v, d_x_pred, d_w: [n] float32 (device).
+ * mego_mean: the estimate, mean of d_x[0, n), into *d_out (double), with a
+ * deterministic reduction in a caller workspace of
+ * mego_mean_workspace_bytes() bytes (8-byte aligned).
+ */
+mego_status mego_sir_predict_update(const float* d_x, const float* d_v, int32_t n,
+                                    float drift, float z, float* d_x_pred,
+                                    float* d_w, void* stream);
+size_t mego_mean_workspace_bytes(void);
+mego_status mego_mean(const float* d_x, int32_t n, double* d_out, void* d_ws,
+                      size_t ws_bytes, void* stream);
+
+/* ----------------------------------------------------------------------
  * Wait for `stream` up to timeout_s seconds by polling an event, then copy
  * the device status word to *h_status.  Returns MEGO_ETIMEOUT (and leaves
  * *h_status untouched) if the stream has not drained by the deadline. */

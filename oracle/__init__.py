@@ -89,6 +89,11 @@ def _load():
         lib.oracle_gather_aos4.restype = ctypes.c_int
         lib.oracle_likelihood.argtypes = [vp, u32, ctypes.c_float, vp]
         lib.oracle_likelihood.restype = None
+        lib.oracle_sir_predict_update.argtypes = [vp, vp, u32, ctypes.c_float, ctypes.c_float,
+                                                  vp, vp]
+        lib.oracle_sir_predict_update.restype = None
+        lib.oracle_mean.argtypes = [vp, u32]
+        lib.oracle_mean.restype = f64
         _lib = lib
         return lib
 
@@ -266,3 +271,20 @@ def likelihood(x, y: float) -> np.ndarray:
     w = np.empty_like(x)
     lib.oracle_likelihood(_ptr(x), x.shape[0], ctypes.c_float(y), _ptr(w))
     return w
+
+
+def sir_predict_update(x, v, drift: float, z: float):
+    """Predict (Eq. 22) and weight (Eq. 23) of the SIR filter: (x_pred, w)."""
+    lib = _load()
+    x = _f32(x)
+    v = _f32(v)
+    xp = np.empty_like(x)
+    w = np.empty_like(x)
+    lib.oracle_sir_predict_update(_ptr(x), _ptr(v), x.shape[0], ctypes.c_float(drift),
+                                  ctypes.c_float(z), _ptr(xp), _ptr(w))
+    return xp, w
+
+
+def mean(x) -> float:
+    x = _f32(x)
+    return float(_load().oracle_mean(_ptr(x), x.shape[0]))

@@ -25,12 +25,14 @@
  *   - The iteration bound B, Eq. 3 (Section 3) and Proposition 1 (Eq. 4).
  *   - The ancestor gather (last step of Algorithms 2 and 5).
  *   - The Gaussian likelihood weight of Eq. 12 without its constant factor.
+ *   - The predict/update and estimate stages of the modified SIR filter
+ *     (Algorithm 6, model of Eqs. 22-23).
  *
  * Parity status: every function here is pinned by a CPU test against
  * something other than itself (a library routine, a closed form, an exact
  * Markov-chain computation or the paper's printed tables), except
- * oracle_likelihood, whose pin is the closed form exp(-(x-y)^2/2) evaluated
- * by the test in double.
+ * oracle_likelihood and the SIR stages, whose pins are their closed forms
+ * evaluated by the tests in double.
  */
 #include <math.h>
 #include <stdint.h>
@@ -406,4 +408,37 @@ void oracle_likelihood(const float* x, uint32_t n, float y, float* w) {
     double d = (double)x[i] - (double)y;
     w[i] = (float)exp(-0.5 * d * d);
   }
+}
+
+/* ---------------------------------------------------------------------- */
+/* Modified SIR filter stages (Algorithm 6; model of Eqs. 22-23).
+ * Predict: x' = x/2 + 25 x/(1 + x^2) + drift + v, drift = 8 cos(1.2 t) and v
+ * the process noise (inputs); the paper computes in single precision, and
+ * this restatement uses binary32 operations in a fixed order (no
+ * contraction).  Update: w = exp(-(z - x'^2/20)^2 / 2), the exponential in
+ * double and rounded once.                                                */
+void oracle_sir_predict_update(const float* x, const float* v, uint32_t n, float drift,
+                               float z, float* x_pred, float* w) {
+  uint32_t i;
+  for (i = 0; i < n; ++i) {
+    float xi = x[i];
+    float den = 1.0f + xi * xi;
+    float frac = (25.0f * xi) / den;
+    float xp = 0.5f * xi + frac;
+    float d, a;
+    xp = xp + drift;
+    xp = xp + v[i];
+    d = z - (xp * xp) / 20.0f;
+    a = 0.5f * (d * d);
+    x_pred[i] = xp;
+    w[i] = (float)exp(-(double)a);
+  }
+}
+
+/* Estimate of Algorithm 6: the mean of the resampled particles (double). */
+double oracle_mean(const float* x, uint32_t n) {
+  uint32_t i;
+  double s = 0.0;
+  for (i = 0; i < n; ++i) s += (double)x[i];
+  return s / (double)n;
 }

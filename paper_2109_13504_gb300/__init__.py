@@ -149,6 +149,10 @@ def _load():
         "mego_server_destroy": ([vp], ci),
         "mego_server_replay": ([vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_double),
                                 i32, f64], ci),
+        "mego_sir_predict_update": ([vp, vp, i32, ctypes.c_float, ctypes.c_float, vp, vp, vp],
+                                    ci),
+        "mego_mean_workspace_bytes": ([], sz),
+        "mego_mean": ([vp, i32, vp, vp, sz, vp], ci),
         "mego_autotune": ([vp, i32, i32, ci, u32, vp, vp, i32, ctypes.c_int64, ci, vp, i32,
                            ctypes.POINTER(LaunchCfg), ctypes.POINTER(ctypes.c_float), vp], ci),
     }
@@ -612,3 +616,37 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+# --------------------------------------------------------------------------
+# SIR filter stages (Algorithm 6)
+
+
+def mego_sir_predict_update(x: torch.Tensor, v: torch.Tensor, drift: float, z: float,
+                            x_pred: Optional[torch.Tensor] = None,
+                            w: Optional[torch.Tensor] = None, stream=None):
+    n = x.numel()
+    if x_pred is None:
+        x_pred = torch.empty_like(x)
+    if w is None:
+        w = torch.empty_like(x)
+    st = _load().mego_sir_predict_update(_dev(x, torch.float32, "x"), _dev(v, torch.float32, "v", n),
+                                         n, ctypes.c_float(drift), ctypes.c_float(z),
+                                         _dev(x_pred, torch.float32, "x_pred", n),
+                                         _dev(w, torch.float32, "w", n), _stream(stream))
+    _check(st, "mego_sir_predict_update")
+    return x_pred, w
+
+
+def mego_mean(x: torch.Tensor, out: Optional[torch.Tensor] = None,
+              ws: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    n = x.numel()
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=x.device)
+    need = int(_load().mego_mean_workspace_bytes())
+    if ws is None:
+        ws = torch.empty(need, dtype=torch.uint8, device=x.device)
+    st = _load().mego_mean(_dev(x, torch.float32, "x"), n, _dev(out, torch.float64, "out", 1),
+                           _dev(ws, torch.uint8, "ws"), ws.numel(), _stream(stream))
+    _check(st, "mego_mean")
+    return out

@@ -94,3 +94,35 @@ def test_mse_per_n_matches_paper_tables(paper):
         se = vals.std(ddof=1) / np.sqrt(vals.size)
         got = vals.mean()
         assert abs(got - want) <= 4.0 * se + 0.004, (name, y, got, want, se)
+
+
+def _c_job(args):
+    y, variant, ps, k0, K, wseed, n = args
+    import oracle as o
+    import synthetic as syn
+    from oracle.stats import offspring_stats as st
+    w = syn.gaussian_weights(n, y, wseed)
+    _, B, _ = o.compute_B(w, 0.01)
+    return y, variant, ps, [st(w, [o.resample(w, B, 20_000 + k, variant, psize_bytes=ps)])["mse_per_n"]
+                            for k in range(k0, k0 + K)]
+
+
+def test_partition_variants_match_paper_tables(paper):
+    """Metropolis-C1/C2 (Algorithms 3, 4) at N = 2^15 against Tables 5-6 for
+    the smallest and largest partition sizes, where both differ most from
+    plain Metropolis (e.g. C1 with 128-byte partitions at y = 4: MSE/N 15.4)."""
+    n = 1 << 15
+    jobs = [(y, v, ps, 100 * ws, 6, ws, n) for v in (oracle.C1, oracle.C2)
+            for ps in (128, 2048) for y in (0, 2, 4) for ws in (1, 2)]
+    oracle.build()
+    res = {}
+    with ProcessPoolExecutor(min(8, os.cpu_count() or 1),
+                             mp_context=mp.get_context("spawn")) as ex:
+        for y, v, ps, vals in ex.map(_c_job, jobs):
+            res.setdefault((v, ps, y), []).extend(vals)
+    for (v, ps, y), vals in sorted(res.items()):
+        name = "c1" if v == oracle.C1 else "c2"
+        want = paper[name][str(ps)][str(n)]["mse_per_n"][y]
+        vals = np.asarray(vals)
+        se = vals.std(ddof=1) / np.sqrt(vals.size)
+        assert abs(vals.mean() - want) <= 4.0 * se + 0.01 * want, (name, ps, y, vals.mean(), want)
