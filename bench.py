@@ -648,6 +648,7 @@ PROFILE_CASES = {
     "mego_global_n2p24_y4": ("megopolis", 24, 4, "global", None),
     "mego_gather6_n2p20_y2": ("megopolis", 20, 2, "global", "soa6"),
     "bound_n2p20": ("bound", 20, 2, None, None),
+    "batch512": ("batch", 0, 0, None, None),
 }
 
 
@@ -660,8 +661,21 @@ def run_case(name: str):
     import synthetic
 
     kind, log2n, y, path, gather = PROFILE_CASES[name]
-    n = 1 << log2n
     dev = torch.device("cuda:0")
+    if kind == "batch":
+        sizes, ys = synthetic.filter_sizes(512, 8.0, 16.0, 4)
+        ws = [torch.from_numpy(synthetic.gaussian_weights(int(m), float(yy), 40 + f)).to(dev)
+              for f, (m, yy) in enumerate(zip(sizes, ys))]
+        filters = [{"w": w, "anc": torch.empty(w.numel(), dtype=torch.int32, device=dev),
+                    "B": -1, "stream_id": f} for f, w in enumerate(ws)]
+        batch = mego.Batch(filters, seed=SEED)
+        for _ in range(4):
+            batch.bound(EPS)
+            batch.resample()
+        torch.cuda.synchronize()
+        print(json.dumps({"case": name, "filters": 512, "particles": int(sum(sizes))}))
+        return
+    n = 1 << log2n
     w = torch.from_numpy(synthetic.gaussian_weights(n, y, SEED + y)).to(dev)
     B_dev, status, _ = mego.mego_compute_B(w, EPS)
     B = int(B_dev.item())
