@@ -354,6 +354,44 @@ def _sir_leg(args, mego, synthetic, torch, dev):
     return out
 
 
+def _sweep_leg(args, mego, synthetic, torch, dev):
+    """The scaling sweep: resample time (B computed beforehand, as the
+    paper's Tables 3-4 exclude it) at N = 2^14..2^24 and y = 0..4, Megopolis
+    and Metropolis, each with its autotuned launch shape; median of a few
+    event-timed launches, L2 flushed before each."""
+    import statistics as stats
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    for log2n in (14, 16, 18, 20, 22, 24):
+        n = 1 << log2n
+        anc = torch.empty(n, dtype=torch.int32, device=dev)
+        row = {}
+        for y in range(5):
+            w = torch.from_numpy(synthetic.gaussian_weights(n, y, SEED + y)).to(dev)
+            B_dev, _, _ = mego.mego_compute_B(w, EPS, stream=stream)
+            B = int(B_dev.item())
+            cell = {"B": B}
+            for variant, name in ((mego.MEGOPOLIS, "megopolis"), (mego.METROPOLIS, "metropolis")):
+                cfg, _ = mego.mego_autotune(w, B, variant, anc=anc, reps=2, stream=stream)
+                ts = []
+                for _ in range(args.sweep_reps):
+                    flush.zero_()
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    mego.mego_resample_gather(w, B, None, SEED, 0, variant, anc=anc, cfg=cfg,
+                                              stream=stream)
+                    b.record(stream)
+                    torch.cuda.synchronize(dev)
+                    ts.append(a.elapsed_time(b))
+                cell[name + "_ms"] = stats.median(ts)
+            cell["speedup"] = cell["metropolis_ms"] / cell["megopolis_ms"]
+            row[str(y)] = cell
+            del w
+        out[str(n)] = row
+    return out
+
+
 def run_reference(args):
     """The reference arm: the CPU oracle as it stands, timed on the host."""
     world, rank, _ = _dist()
@@ -563,6 +601,7 @@ def run_gpu(args):
     batched = _batched_leg(args, mego, synthetic, torch, dev)
     serving = _serving_leg(args, mego, synthetic, torch, dev) if args.serve_requests > 0 else None
     sir = _sir_leg(args, mego, synthetic, torch, dev) if args.sir_trajectories > 0 else None
+    sweep = _sweep_leg(args, mego, synthetic, torch, dev) if args.sweep_reps > 0 else None
 
     if rank != 0:
         if dist is not None:
@@ -628,6 +667,7 @@ def run_gpu(args):
         "batched": batched,
         "serving": serving,
         "sir_filter": sir,
+        "scaling_sweep_resample_ms": sweep,
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": 4 * N * len(YS),
@@ -710,6 +750,8 @@ def main():
     ap.add_argument("--sir-trajectories", type=int, default=4,
                     help="trajectories in the SIR filter leg (0 skips it)")
     ap.add_argument("--sir-runs", type=int, default=4)
+    ap.add_argument("--sweep-reps", type=int, default=7,
+                    help="timed launches per cell of the N x y sweep (0 skips it)")
     ap.add_argument("--case", choices=sorted(PROFILE_CASES),
                     help="run one kernel case (for profilers) instead of the benchmark")
     args = ap.parse_args()
