@@ -380,6 +380,15 @@ mego_status mego_autotune(const float* d_w, int32_t n, int32_t B, int variant,
                           float* best_ms, void* stream);
 
 /* ----------------------------------------------------------------------
+ * Device faults of the resample kernels: the shared-memory path waits for
+ * its bulk copy of the weights with a bounded number of polls; if the copy
+ * has not landed by then, the CTA records a fault (1) and writes nothing.
+ * *h_fault receives the OR of the recorded faults since the last call
+ * (0: none), and the record is cleared.  Synchronises the device.
+ */
+mego_status mego_device_fault(int32_t* h_fault);
+
+/* ----------------------------------------------------------------------
  * Measurement helper (not part of the method): read `bytes` of d_buf
  * `reps` times with coalesced 128-bit loads, writing one float per CTA to
  * d_sink (at least four floats per SM) so the reads are not elided.  Used to

@@ -130,6 +130,7 @@ def _load():
                                 sz, vp], ci),
         "mego_sync_status": ([vp, vp, f64, vp], ci),
         "mego_probe_read": ([vp, sz, i32, vp, vp], ci),
+        "mego_device_fault": ([vp], ci),
         "mego_batch_plan_bytes": ([ctypes.POINTER(Filter), i32], sz),
         "mego_batch_plan": ([ctypes.POINTER(Filter), i32, ci, ci, u64, vp, sz,
                              ctypes.POINTER(BatchHandle), vp], ci),
@@ -397,6 +398,13 @@ def mego_autotune(w: torch.Tensor, B: int, variant: int = MEGOPOLIS, psize_bytes
     _check(st, "mego_autotune")
     return ({"threads": best.threads, "ppt": best.ppt, "path": best.path,
              "ctas_per_sm": best.ctas_per_sm}, float(ms.value))
+
+
+def mego_device_fault() -> int:
+    """OR of the faults recorded by the resample kernels since the last call."""
+    h = ctypes.c_int32(-1)
+    _check(_load().mego_device_fault(ctypes.addressof(h)), "mego_device_fault")
+    return int(h.value)
 
 
 def mego_probe_read(buf: torch.Tensor, reps: int, sink: torch.Tensor, stream=None) -> None:

@@ -526,6 +526,24 @@ mego_status mego_autotune(const float* d_w, int32_t n, int32_t B, int variant,
   return MEGO_OK;
 }
 
+mego_status mego_device_fault(int32_t* h_fault) {
+  if (!h_fault) return MEGO_EINVAL;
+  int32_t* words[4] = {mego::resample_fault_word<mego::kMegopolis>(),
+                       mego::resample_fault_word<mego::kMetropolis>(),
+                       mego::resample_fault_word<mego::kC1>(),
+                       mego::resample_fault_word<mego::kC2>()};
+  int32_t any = 0;
+  for (int32_t* w : words) {
+    if (!w) return MEGO_ECUDA;
+    int32_t v = 0;
+    if (cudaMemcpy(&v, w, sizeof v, cudaMemcpyDeviceToHost) != cudaSuccess) return MEGO_ECUDA;
+    any |= v;
+    if (v && cudaMemset(w, 0, sizeof v) != cudaSuccess) return MEGO_ECUDA;
+  }
+  *h_fault = any;
+  return MEGO_OK;
+}
+
 mego_status mego_probe_read(const void* d_buf, size_t bytes, int32_t reps, float* d_sink,
                             void* stream) {
   if (!d_buf || !d_sink || bytes < 16u || bytes % 16u || reps < 1) return MEGO_EINVAL;

@@ -3,10 +3,33 @@
 // Included once per variant translation unit, with MEGO_VARIANT defined.
 #pragma once
 
+#include <mutex>
+
 #include "resample_kernels.cuh"
 
 namespace mego {
 namespace {
+
+// Fault word of this variant's kernels (set when the shared-memory staging
+// gives up waiting for its bulk copy); read and cleared by mego_device_fault.
+__device__ int32_t g_fault_word;
+
+int32_t* fault_word_address() {
+  static std::mutex mu;
+  static int32_t* addr[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_fault_word) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    addr[dev] = static_cast<int32_t*>(p);
+  }
+  return addr[dev];
+}
 
 template <int V, int P, bool S, int G>
 cudaError_t launch_one(const LaunchShape& s, const ResampleArgs& a, cudaStream_t st) {
@@ -71,8 +94,15 @@ const void* ptr_by_gather(int ppt, int gather) {
 template <>
 cudaError_t launch_resample<MEGO_VARIANT>(const LaunchShape& s, int gather,
                                           const ResampleArgs& a, cudaStream_t st) {
-  return s.smem ? by_gather<MEGO_VARIANT, true>(s, gather, a, st)
-                : by_gather<MEGO_VARIANT, false>(s, gather, a, st);
+  if (!s.smem) return by_gather<MEGO_VARIANT, false>(s, gather, a, st);
+  ResampleArgs b = a;
+  b.p.fault = fault_word_address();
+  return by_gather<MEGO_VARIANT, true>(s, gather, b, st);
+}
+
+template <>
+int32_t* resample_fault_word<MEGO_VARIANT>() {
+  return fault_word_address();
 }
 
 template <>

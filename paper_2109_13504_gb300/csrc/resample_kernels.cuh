@@ -446,4 +446,8 @@ cudaError_t launch_resample(const LaunchShape& s, int gather, const ResampleArgs
 template <int VARIANT>
 const void* resample_kernel_ptr(int ppt, bool smem, int gather);
 
+// Device address of the variant's fault word (for the current device).
+template <int VARIANT>
+int32_t* resample_fault_word();
+
 }  // namespace mego

@@ -335,3 +335,11 @@ def test_autotune_picks_a_shape_and_keeps_results_exact():
     for ppt in (1, 2, 4, 8):
         got = _anc(w_h, 60, 5, mego.MEGOPOLIS, cfg={"ppt": ppt, "threads": 128})
         assert np.array_equal(got, oracle.resample(w_h, 60, 5, mego.MEGOPOLIS))
+
+
+def test_no_device_faults_after_the_shared_memory_path():
+    n = 9000
+    w_h = synthetic.gaussian_weights(n, 2.0, 3)
+    for v in VARIANTS:
+        _anc(w_h, 10, 1, v, cfg={"path": mego.PATH_SMEM})
+    assert mego.mego_device_fault() == 0
