@@ -43,9 +43,8 @@ YS = (0, 1, 2, 3, 4)
 EPS = 0.01
 SEED = 1
 FLUSH_BYTES = 256 << 20
-PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "megopolis_resample_n2p20_y4.md")
-KERNEL_SOURCES = ("resample_kernels.cuh", "device_common.cuh", "resample_dispatch.cuh",
-                  "resample_megopolis.cu")
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "batch_resample_sweep5_n2p20.md")
+KERNEL_SOURCES = ("resample_kernels.cuh", "device_common.cuh", "batch.cu")
 
 
 def _peaks():
@@ -506,6 +505,43 @@ def run_gpu(args):
             step_ms.append(tot)
         return step_ms, per_y, kern, launches
 
+    # The main step: the five vectors as one batch (batched bound + one
+    # persistent resample launch), captured in a CUDA graph on a side stream.
+    side = torch.cuda.Stream(dev)
+
+    def make_batch(variant):
+        filters = [{"w": w_dev[t], "anc": anc[t], "B": -1, "stream_id": 0}
+                   for t in range(len(YS))]
+        with torch.cuda.stream(side):
+            b = mego.Batch(filters, variant=variant, seed=SEED, stream=side)
+            b.bound(EPS, stream=side)
+            b.resample(stream=side)
+            b.autotune(reps=3, stream=side)
+            b.capture(EPS, stream=side)
+        side.synchronize()
+        return b
+
+    def timed_batch(b, steps, warmup):
+        for _ in range(warmup):
+            b.replay(stream=side)
+        side.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        l0 = mego.launch_count()
+        torch.cuda.nvtx.range_push("timed_batch")
+        with torch.cuda.stream(side):
+            for s_ in range(steps):
+                flush.zero_()
+                evs[s_][0].record(side)
+                b.replay(stream=side)
+                evs[s_][1].record(side)
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize(dev)
+        return [a.elapsed_time(e) for a, e in evs], mego.launch_count() - l0
+
     # Launch shapes: autotune each variant on the workload (outside the timed
     # region), the largest B last, since the device-side bound launches use
     # the shape tuned last for their size bucket.
@@ -526,16 +562,29 @@ def run_gpu(args):
             raise RuntimeError("device bound failed for y=%d" % YS[t])
         Bs.append(int(B_dev[t].item()))
 
+    batch_mego = make_batch(mego.MEGOPOLIS)
+    batch_metro = make_batch(mego.METROPOLIS)
+    batch_shape = batch_mego.shape
     sampler = ClockSampler(dev.index)
     sampler.start()
     time.sleep(0.3)
-    mego_ms, mego_y, mego_kern, launches = timed(mego.MEGOPOLIS, args.steps, args.warmup)
+    bstep_ms, launches = timed_batch(batch_mego, args.steps, args.warmup)
     metro_steps = max(3, args.steps // 4)
+    bmetro_ms, _ = timed_batch(batch_metro, metro_steps, args.warmup)
+    mego_ms, mego_y, mego_kern, _ = timed(mego.MEGOPOLIS, args.steps, args.warmup)
     metro_ms, metro_y, _, _ = timed(mego.METROPOLIS, metro_steps, args.warmup)
     clocks = sampler.stop()
+    # Kernel time of the batched resample (the dominant kernel), from events
+    # around a replay of a graph holding only the resample.
+    with torch.cuda.stream(side):
+        batch_mego.capture(0.0, stream=side)
+    bk_ms, _ = timed_batch(batch_mego, max(5, args.steps // 4), 2)
+    batch_mego.close()
+    batch_metro.close()
 
-    total_ms, particles = replica_aggregate(sum(mego_ms), N * len(YS) * args.steps, dist, dev)
+    total_ms, particles = replica_aggregate(sum(bstep_ms), N * len(YS) * args.steps, dist, dev)
     value = particles / (total_ms / 1e3)
+    seq_value = N * len(YS) * args.steps / (sum(mego_ms) / 1e3)
     metro_value = N * len(YS) * metro_steps / (sum(metro_ms) / 1e3)
 
     # Roofline of the dominant kernel: Megopolis at y = 4.  It is bound by
@@ -544,14 +593,14 @@ def run_gpu(args):
     # per SM-cycle x SM clock / 3.75 multiplies per proposal (15 of the 20
     # multiplies of a 4-word Philox call vary with the iteration).
     hbm_peak, peak_src = _peaks()
-    B4 = Bs[-1]
-    k_ms = statistics.mean(mego_kern)
-    alg_bytes = N * (4.0 * B4 + 8.0)
+    k_ms = statistics.mean(bk_ms)
+    sumB = float(sum(Bs))
+    alg_bytes = N * (4.0 * sumB + 8.0 * len(YS))
     achieved_gbs = alg_bytes / (k_ms / 1e3) / 1e9
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     clk_mhz = clocks.get("sm_max_mhz") or 2070.0
     peak_gprop = sms * 32.0 * clk_mhz * 1e6 / 3.75 / 1e9
-    achieved_gprop = N * B4 / (k_ms / 1e3) / 1e9
+    achieved_gprop = N * sumB / (k_ms / 1e3) / 1e9
     sink = torch.empty(4096, dtype=torch.float32, device=dev)
     probe_buf = torch.empty(32 << 20, dtype=torch.uint8, device=dev)
     mego.mego_probe_read(probe_buf, 16, sink, stream=stream)
@@ -583,19 +632,24 @@ def run_gpu(args):
         if s >= args.warmup:
             fused.append(a.elapsed_time(b))
 
-    # End to end through the host-buffer C-ABI call (copies inside the region).
+    # End to end through the public host-buffer API: every step submits the
+    # five vectors (page-locked host memory) to the serving loop, which
+    # uploads them, runs one batched launch, copies the ancestors back, and
+    # the step ends when all five are on the host.
     h_w = [torch.from_numpy(synthetic.gaussian_weights(N, y, SEED + y)).pin_memory() for y in YS]
-    h_anc = torch.empty(N, dtype=torch.int32).pin_memory()
-    d_sc = torch.empty(32, dtype=torch.uint8, device=dev)
+    h_anc = [torch.empty(N, dtype=torch.int32).pin_memory() for _ in YS]
+    server = mego.Server(arena_bytes=256 << 20, seed=SEED, max_batch=len(YS), streams=2,
+                         with_state=False, device=dev)
     e2e_steps = max(3, args.steps // 4)
-    for s in range(args.warmup + e2e_steps):
-        if s == args.warmup:
-            torch.cuda.synchronize(dev)
+    for s_ in range(args.warmup + e2e_steps):
+        if s_ == args.warmup:
             t0 = time.perf_counter()
         for t in range(len(YS)):
-            mego.mego_resample_host(h_w[t], -1, EPS, SEED, 0, mego.MEGOPOLIS, h_anc, w_dev[t],
-                                    anc[t], d_sc, ws[t], stream=stream)
+            server.submit(s_ * len(YS) + t, h_w[t], None, h_anc[t], None)
+        server.drain(60.0)
+        server.poll()
     e2e_s = time.perf_counter() - t0
+    server.close()
     e2e_value = N * len(YS) * e2e_steps / e2e_s
 
     batched = _batched_leg(args, mego, synthetic, torch, dev)
@@ -624,6 +678,8 @@ def run_gpu(args):
         "steps": args.steps,
         "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps,
+        "p50_ms_per_step": pct(bstep_ms, 50),
+        "p99_ms_per_step": pct(bstep_ms, 99),
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
@@ -632,15 +688,24 @@ def run_gpu(args):
         "config": {"workload": "scaling sweep at N=2^20: y=0..4 (x~N(0,1), "
                                "w=exp(-(x-y)^2/2)), B from Eq. 3 at eps=0.01 on the device, "
                                "Megopolis, int32 ancestors",
+                   "execution": "the five vectors as one batch per step: batched bound + one "
+                                "persistent resample launch, replayed as a CUDA graph",
                    "N": N, "B": dict(zip(map(str, YS), Bs)), "eps": EPS,
                    "l2": "256 MiB buffer written between timed steps",
                    "parallelism": "replicas" if world > 1 else "single GPU",
-                   "launch_shape": {"megopolis": tuned[mego.MEGOPOLIS],
-                                    "metropolis": tuned[mego.METROPOLIS]}},
-        "p50_ms_per_resample": {str(y): pct(mego_y[t], 50) for t, y in enumerate(YS)},
-        "p99_ms_per_resample": {str(y): pct(mego_y[t], 99) for t, y in enumerate(YS)},
+                   "launch_shape": {"batched_megopolis": batch_shape,
+                                    "sequential_megopolis": tuned[mego.MEGOPOLIS],
+                                    "sequential_metropolis": tuned[mego.METROPOLIS]}},
+        "sequential": {
+            "note": "each vector on its own: mego_compute_B + mego_resample_gather, one stream",
+            "value": seq_value, "unit": UNIT, "ms_per_step": statistics.mean(mego_ms),
+            "p50_ms_per_resample": {str(y): pct(mego_y[t], 50) for t, y in enumerate(YS)},
+            "p99_ms_per_resample": {str(y): pct(mego_y[t], 99) for t, y in enumerate(YS)}},
         "metropolis": {
-            "value": metro_value, "unit": UNIT, "ms_per_step": statistics.mean(metro_ms),
+            "value": N * len(YS) * metro_steps / (sum(bmetro_ms) / 1e3), "unit": UNIT,
+            "ms_per_step": statistics.mean(bmetro_ms),
+            "megopolis_speedup": statistics.mean(bmetro_ms) / statistics.mean(bstep_ms),
+            "sequential_value": metro_value,
             "p50_ms_per_resample": {str(y): pct(metro_y[t], 50) for t, y in enumerate(YS)},
             "p99_ms_per_resample": {str(y): pct(metro_y[t], 99) for t, y in enumerate(YS)},
             "megopolis_speedup_per_y": {str(y): statistics.median(metro_y[t]) /
@@ -653,8 +718,8 @@ def run_gpu(args):
         "roofline": {"bound": "alu", "achieved": achieved_gprop, "peak": peak_gprop,
                      "unit": "Gproposals/s", "frac": achieved_gprop / peak_gprop,
                      "traffic": _profiled_traffic(),
-                     "kernel": "Megopolis resample, N=2^20, y=4, B=%d, %.1f us/launch"
-                               % (B4, 1e3 * k_ms),
+                     "kernel": "batched Megopolis resample of the five vectors "
+                               "(N=2^20 each, B=%s), %.1f us/launch" % (Bs, 1e3 * k_ms),
                      "peak_derivation": "%d SMs x 32 32x32->64-bit multiplies per SM-cycle "
                                         "(FMA-heavy pipe) x %.0f MHz / 3.75 multiplies per "
                                         "proposal" % (sms, clk_mhz),
@@ -671,7 +736,9 @@ def run_gpu(args):
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": 4 * N * len(YS),
-                "d2h_bytes_per_step": (4 * N + 8) * len(YS)},
+                "d2h_bytes_per_step": 4 * N * len(YS),
+                "path": "mego_server_submit x5 + drain per step (host buffers, one batched "
+                        "launch, uploads and downloads inside the timed region)"},
         "gpu_launches": launches,
         "cpu_baseline": cpu,
     }
@@ -689,6 +756,7 @@ PROFILE_CASES = {
     "mego_gather6_n2p20_y2": ("megopolis", 20, 2, "global", "soa6"),
     "bound_n2p20": ("bound", 20, 2, None, None),
     "batch512": ("batch", 0, 0, None, None),
+    "batch_sweep5": ("batch5", 20, 0, None, None),
 }
 
 
@@ -702,6 +770,19 @@ def run_case(name: str):
 
     kind, log2n, y, path, gather = PROFILE_CASES[name]
     dev = torch.device("cuda:0")
+    if kind == "batch5":
+        n = 1 << log2n
+        ws = [torch.from_numpy(synthetic.gaussian_weights(n, yy, SEED + yy)).to(dev) for yy in YS]
+        filters = [{"w": w, "anc": torch.empty(n, dtype=torch.int32, device=dev), "B": -1,
+                    "stream_id": 0} for w in ws]
+        batch = mego.Batch(filters, seed=SEED)
+        for _ in range(4):
+            batch.bound(EPS)
+            batch.resample()
+        torch.cuda.synchronize()
+        print(json.dumps({"case": name, "filters": len(YS), "n": n,
+                          "B": batch.B.cpu().tolist()}))
+        return
     if kind == "batch":
         sizes, ys = synthetic.filter_sizes(512, 8.0, 16.0, 4)
         ws = [torch.from_numpy(synthetic.gaussian_weights(int(m), float(yy), 40 + f)).to(dev)

@@ -247,6 +247,7 @@ typedef struct mego_batch {
   mego_launch_cfg cfg; /* threads and particles per thread of the launch      */
   int32_t grid;
   void* graph_exec;    /* captured graph, or NULL                             */
+  int32_t graph_kernels; /* kernels in the captured graph                     */
 } mego_batch;
 
 size_t mego_batch_plan_bytes(const mego_filter* h_filters, int32_t count);

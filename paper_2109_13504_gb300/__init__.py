@@ -71,7 +71,8 @@ class BatchHandle(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("total_items", ctypes.c_uint64),
                 ("total_chunks", ctypes.c_uint64), ("d_B", ctypes.c_void_p),
                 ("d_status", ctypes.c_void_p), ("d_q", ctypes.c_void_p),
-                ("cfg", LaunchCfg), ("grid", ctypes.c_int32), ("graph_exec", ctypes.c_void_p)]
+                ("cfg", LaunchCfg), ("grid", ctypes.c_int32), ("graph_exec", ctypes.c_void_p),
+                ("graph_kernels", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):

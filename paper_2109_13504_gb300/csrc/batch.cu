@@ -486,6 +486,7 @@ mego_status mego_batch_bound(const mego_batch* b, double eps, int32_t b_max, voi
   const unsigned fgrid = static_cast<unsigned>((b->count + 7) / 8);
   batch_finalize_kernel<<<fgrid, 256, 0, st>>>(a, std::log(eps), b_max);
   if (cudaGetLastError() != cudaSuccess) return MEGO_ECUDA;
+  count_launches(2);
   return MEGO_OK;
 }
 
@@ -496,6 +497,7 @@ mego_status mego_batch_resample(const mego_batch* b, void* stream) {
   if (launch_batch(b->variant, b->gather, b->cfg.ppt, b->grid, b->cfg.threads, a,
                    static_cast<cudaStream_t>(stream)) != cudaSuccess)
     return MEGO_ECUDA;
+  count_launches(1);
   return MEGO_OK;
 }
 
@@ -574,6 +576,10 @@ mego_status mego_batch_graph(mego_batch* b, double eps, int32_t b_max, void* str
   mego_status s = MEGO_OK;
   if (eps > 0.0) s = mego_batch_bound(b, eps, b_max, stream);
   if (s == MEGO_OK) s = mego_batch_resample(b, stream);
+  // Captured, not run: take the capture's launches back out of the count.
+  const int32_t kernels = (eps > 0.0 ? 2 : 0) + 1;
+  mego::count_launches(static_cast<uint64_t>(-static_cast<int64_t>(kernels)));
+  b->graph_kernels = kernels;
   cudaGraph_t g = nullptr;
   const cudaError_t e = cudaStreamEndCapture(st, &g);
   if (s != MEGO_OK) {
@@ -594,6 +600,7 @@ mego_status mego_batch_launch_graph(const mego_batch* b, void* stream) {
   if (cudaGraphLaunch(static_cast<cudaGraphExec_t>(b->graph_exec),
                       static_cast<cudaStream_t>(stream)) != cudaSuccess)
     return MEGO_ECUDA;
+  mego::count_launches(static_cast<uint64_t>(b->graph_kernels));
   return MEGO_OK;
 }
 

@@ -18,6 +18,7 @@ struct Partial {
 static_assert(sizeof(Partial) == 16, "partial layout");
 
 int reduce_grid(uint32_t n);
+void count_launches(uint64_t k);
 cudaError_t launch_partials(const float* src, uint32_t n, bool likelihood, float y,
                             float* w_out, Partial* parts, int grid, cudaStream_t st);
 cudaError_t launch_finalize(const Partial* parts, int nparts, uint32_t n, double eps,

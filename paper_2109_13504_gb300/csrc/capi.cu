@@ -222,6 +222,8 @@ mego_status check_partition(int variant, uint32_t n, uint32_t psize, uint32_t* n
 
 namespace mego {
 
+void count_launches(uint64_t k) { g_launches.fetch_add(k); }
+
 cudaError_t enable_large_smem(const void* kernel) {
   static std::mutex mu;
   static std::map<std::pair<int, const void*>, cudaError_t> done;

@@ -68,5 +68,6 @@ extern "C" mego_status mego_compute_B_noalloc(const float* d_w, int32_t n, doubl
   if (mego::launch_finalize(parts, grid, un, eps, b_max, d_B, d_status, d_q, st) !=
       cudaSuccess)
     return MEGO_ECUDA;
+  mego::count_launches(2);
   return MEGO_OK;
 }

@@ -430,6 +430,9 @@ struct LaunchShape {
   size_t smem_bytes;
 };
 
+// Host-side count of kernel launches (capi.cu), reported by mego_launch_count.
+void count_launches(uint64_t k);
+
 // Host helpers (capi.cu): round keys of a seed, constants of a stream.
 RoundKeys make_round_keys(uint64_t seed);
 StreamKey make_stream_key(const RoundKeys& K, uint32_t sid);

@@ -7,6 +7,10 @@
 
 #include "../../include/megopolis.h"
 
+namespace mego {
+void count_launches(uint64_t k);
+}
+
 namespace {
 
 constexpr int kThreads = 256;
@@ -88,7 +92,9 @@ mego_status mego_sir_predict_update(const float* d_x, const float* d_v, int32_t 
   const int grid = grid_for(static_cast<uint32_t>(n), 152 * 8);
   predict_update_kernel<<<grid, kThreads, 0, static_cast<cudaStream_t>(stream)>>>(
       d_x, d_v, static_cast<uint32_t>(n), drift, z, d_x_pred, d_w);
-  return cudaGetLastError() == cudaSuccess ? MEGO_OK : MEGO_ECUDA;
+  if (cudaGetLastError() != cudaSuccess) return MEGO_ECUDA;
+  mego::count_launches(1);
+  return MEGO_OK;
 }
 
 size_t mego_mean_workspace_bytes(void) { return sizeof(double) * kMaxMeanParts + 256u; }
@@ -104,7 +110,9 @@ mego_status mego_mean(const float* d_x, int32_t n, double* d_out, void* d_ws, si
   mean_partials_kernel<<<grid, kThreads, 0, st>>>(d_x, static_cast<uint32_t>(n), parts);
   if (cudaGetLastError() != cudaSuccess) return MEGO_ECUDA;
   mean_finalize_kernel<<<1, 32, 0, st>>>(parts, grid, static_cast<uint32_t>(n), d_out);
-  return cudaGetLastError() == cudaSuccess ? MEGO_OK : MEGO_ECUDA;
+  if (cudaGetLastError() != cudaSuccess) return MEGO_ECUDA;
+  mego::count_launches(2);
+  return MEGO_OK;
 }
 
 }  // extern "C"

@@ -86,7 +86,9 @@ def test_batch_graph_replay_and_shapes_and_autotune():
         for _ in range(3):                 # the work queue resets itself between launches
             for d in filters:
                 d["anc"].fill_(-1)
+            before = mego.launch_count()
             batch.replay(stream=side)
+            assert mego.launch_count() - before == 3     # bound (2) + resample (1)
             side.synchronize()
             assert all(torch.equal(a, d["anc"]) for a, d in zip(ref, filters))
     batch.close()
