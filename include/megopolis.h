@@ -91,7 +91,9 @@ int mego_abi_version(void);
 const char* mego_status_string(int status);
 
 /* ----------------------------------------------------------------------
- * Resample (Algorithm 5 / Algorithm 2 / Algorithms 3-4), B given by the host.
+ * Resample (Algorithm 5 or Algorithm 2), B given by the host.  variant is
+ * MEGO_MEGOPOLIS or MEGO_METROPOLIS; C1/C2 need a partition size and go
+ * through mego_resample_gather.
  *   d_w      [n] float32, finite and >= 0 (not checked here; use
  *            mego_compute_B to validate).  Read-only.
  *   B        number of iterations, 0 <= B <= MEGO_B_MAX; B = 0 gives

@@ -343,3 +343,25 @@ def test_no_device_faults_after_the_shared_memory_path():
     for v in VARIANTS:
         _anc(w_h, 10, 1, v, cfg={"path": mego.PATH_SMEM})
     assert mego.mego_device_fault() == 0
+
+
+@pytest.mark.parametrize("alpha", [0.5, 2.0, 3.0, 10.0, 50.0])
+def test_gamma_weights_bit_exact(alpha):
+    """The paper's second weight generator (Eq. 13, Appendix A): gamma
+    weights with rate 1, both variants, B from the bound."""
+    for n in (40_000, 1 << 18):
+        w_h = synthetic.gamma_weights(n, alpha, 3)
+        w = _gpu(w_h)
+        B_dev, status, _ = mego.mego_compute_B(w, 0.01)
+        st, B_cpu, q_cpu = oracle.compute_B(w_h, 0.01)
+        assert _b_equal(int(B_dev.item()), B_cpu, q_cpu)
+        B = int(B_dev.item())
+        idx = _sample_idx(n, np.random.default_rng(int(alpha * 10)))
+        for v in VARIANTS:
+            anc = torch.empty(n, dtype=torch.int32, device=DEV)
+            mego.mego_resample_gather(w, 0, B_dev, 17, 0, v, anc=anc)
+            got = anc.cpu().numpy()
+            if n <= 40_000:
+                assert np.array_equal(got, oracle.resample(w_h, B, 17, v))
+            else:
+                assert np.array_equal(got[idx], oracle.resample_at(w_h, B, 17, idx, v))
