@@ -42,6 +42,10 @@ N = 1 << 20
 YS = (0, 1, 2, 3, 4)
 EPS = 0.01
 SEED = 1
+# Wide multiplies per Megopolis proposal that vary with the iteration: a
+# Philox4x32-10 call has 20, the kernel hoists the 5 that depend only on the
+# particle and the stream, and one call serves five proposals.
+MULS_PER_PROPOSAL = 15.0 / 5.0
 FLUSH_BYTES = 256 << 20
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "batch_resample_sweep5_n2p20.md")
 KERNEL_SOURCES = ("resample_kernels.cuh", "device_common.cuh", "batch.cu")
@@ -590,8 +594,9 @@ def run_gpu(args):
     # Roofline of the dominant kernel: Megopolis at y = 4.  It is bound by
     # the integer-multiply (FMA-heavy) and ALU pipes that Philox4x32-10 needs,
     # not by memory: peak proposal rate = SMs x 32 wide 32x32-bit multiplies
-    # per SM-cycle x SM clock / 3.75 multiplies per proposal (15 of the 20
-    # multiplies of a 4-word Philox call vary with the iteration).
+    # per SM-cycle x SM clock / 3 multiplies per proposal (15 of the 20
+    # multiplies of a Philox call vary with the iteration, and one call
+    # serves five proposals).
     hbm_peak, peak_src = _peaks()
     k_ms = statistics.mean(bk_ms)
     sumB = float(sum(Bs))
@@ -599,7 +604,7 @@ def run_gpu(args):
     achieved_gbs = alg_bytes / (k_ms / 1e3) / 1e9
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     clk_mhz = clocks.get("sm_max_mhz") or 2070.0
-    peak_gprop = sms * 32.0 * clk_mhz * 1e6 / 3.75 / 1e9
+    peak_gprop = sms * 32.0 * clk_mhz * 1e6 / MULS_PER_PROPOSAL / 1e9
     achieved_gprop = N * sumB / (k_ms / 1e3) / 1e9
     sink = torch.empty(4096, dtype=torch.float32, device=dev)
     probe_buf = torch.empty(32 << 20, dtype=torch.uint8, device=dev)
@@ -721,8 +726,8 @@ def run_gpu(args):
                      "kernel": "batched Megopolis resample of the five vectors "
                                "(N=2^20 each, B=%s), %.1f us/launch" % (Bs, 1e3 * k_ms),
                      "peak_derivation": "%d SMs x 32 32x32->64-bit multiplies per SM-cycle "
-                                        "(FMA-heavy pipe) x %.0f MHz / 3.75 multiplies per "
-                                        "proposal" % (sms, clk_mhz),
+                                        "(FMA-heavy pipe) x %.0f MHz / %.1f multiplies per "
+                                        "proposal" % (sms, clk_mhz, MULS_PER_PROPOSAL),
                      "memory_view": {"algorithmic_bytes_per_launch": alg_bytes,
                                      "achieved_gbs": achieved_gbs,
                                      "hbm_peak_gbs": hbm_peak, "hbm_peak_source": peak_src,

@@ -138,13 +138,19 @@ uint32_t oracle_offset(uint64_t seed, uint32_t sid, uint32_t b, uint32_t n) {
   return uniform_index64(x[0], x[1], n);
 }
 
-/* The uniform u that particle i uses at Megopolis iteration b: four
- * consecutive iterations share one Philox call, iteration b takes word
- * b mod 4 of the call for counter (i, floor(b/4), sid, TAG_MEGO_U).        */
+/* The uniform u that particle i uses at Megopolis iteration b.  Five
+ * consecutive iterations share one Philox call, the one for counter
+ * (i, floor(b/5), sid, TAG_MEGO_U).  With q = b mod 5: q < 4 uses word q;
+ * q = 4 uses the word made of the most significant bytes of words 0, 1
+ * and 2 (in that order, from the least significant byte up).  The u
+ * mapping reads only the low 23 bits of a word, so the five uniforms of a
+ * call are built from disjoint bits.                                       */
 float oracle_megopolis_u(uint64_t seed, uint32_t sid, uint32_t i, uint32_t b) {
   uint32_t x[4];
-  draw(seed, i, b >> 2, sid, TAG_MEGO_U, x);
-  return oracle_u_from_word(x[b & 3u]);
+  uint32_t q = b % 5u;
+  draw(seed, i, b / 5u, sid, TAG_MEGO_U, x);
+  if (q < 4u) return oracle_u_from_word(x[q]);
+  return oracle_u_from_word((x[0] >> 24) | ((x[1] >> 24) << 8) | ((x[2] >> 24) << 16));
 }
 
 /* Proposal and uniform for Metropolis particle i at iteration b: two

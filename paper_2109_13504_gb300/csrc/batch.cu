@@ -464,12 +464,17 @@ mego_status mego_batch_plan(const mego_filter* h_filters, int32_t count, int var
   out->d_B = reinterpret_cast<int32_t*>(static_cast<unsigned char*>(d_plan) + L.B);
   out->d_status = reinterpret_cast<int32_t*>(static_cast<unsigned char*>(d_plan) + L.status);
   out->d_q = reinterpret_cast<double*>(static_cast<unsigned char*>(d_plan) + L.q);
+  // Default shape: Megopolis chains are bound by instruction issue, and four
+  // independent chains per thread (one whole work item per warp) hide the
+  // generator's latency better than more resident warps; Metropolis is bound
+  // by scattered loads and takes two.
+  const int ppt = variant == MEGO_MEGOPOLIS ? 4 : 2;
   out->cfg.threads = 256;
-  out->cfg.ppt = 2;
+  out->cfg.ppt = ppt;
   out->cfg.path = MEGO_PATH_GLOBAL;
   out->cfg.ctas_per_sm = 0;
   int grid = 0;
-  const mego_status s = shape_for(variant, out->gather, 256, 2, &grid);
+  const mego_status s = shape_for(variant, out->gather, 256, ppt, &grid);
   if (s != MEGO_OK) return s;
   out->grid = grid;
   return MEGO_OK;

@@ -144,6 +144,18 @@ __device__ __forceinline__ uint32_t word_of(const uint4& x, int q) {
   return q == 0 ? x.x : (q == 1 ? x.y : (q == 2 ? x.z : x.w));
 }
 
+// Megopolis draws five uniforms from one Philox call: iteration 5 g + q of
+// particle i uses call (i, g, sid, kTagMegoU); q < 4 takes word q (its low 23
+// bits, through u_of); q = 4 takes the word whose bytes 0, 1, 2 are the top
+// bytes (bits 24-31) of words 0, 1, 2 -- bits no other iteration reads.
+constexpr int kMegoPerCall = 5;
+
+__device__ __forceinline__ uint32_t mego_word(const uint4& x, int q) {
+  if (q < 4) return word_of(x, q);
+  // byte_perm selectors: (x.b3, y.b3, -, -), then (that.b0, that.b1, z.b3, -).
+  return __byte_perm(__byte_perm(x.x, x.y, 0x0073u), x.z, 0x0710u);
+}
+
 // ---------------------------------------------------------------------------
 // Bulk async copy global -> shared with mbarrier completion (sm_90+ PTX).
 

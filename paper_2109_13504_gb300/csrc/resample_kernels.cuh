@@ -63,6 +63,19 @@ __device__ __forceinline__ float ldw(const float* __restrict__ w, uint32_t j) {
   }
 }
 
+// w[x0 + off] with the constant off added to the pointer, not to the 32-bit
+// index: the address of (w + x0) is formed once per x0 and each constant off
+// becomes the load's immediate offset.  (An index sum x0 + off in 32 bits may
+// wrap, so the compiler would form a separate 64-bit address for each off.)
+template <bool SMEM>
+__device__ __forceinline__ float ldw_at(const float* __restrict__ w, uint32_t x0, uint32_t off) {
+  if constexpr (SMEM) {
+    return (reinterpret_cast<const float*>(g_dyn_smem) + x0)[off];
+  } else {
+    return __ldg((w + x0) + off);
+  }
+}
+
 // Stage w[0, n) into dynamic shared memory.  Returns false (uniformly for the
 // CTA) if the bulk copy did not complete within the poll budget.
 __device__ __forceinline__ bool stage_weights(const Problem& a) {
@@ -103,7 +116,7 @@ __device__ __forceinline__ void finish_batch(const Problem& a, uint32_t ibase,
                                              const bool (&live)[P]) {
 #pragma unroll
   for (int p = 0; p < P; ++p)
-    if (live[p] && a.anc) a.anc[ibase + 32u * p] = static_cast<int32_t>(k[p]);
+    if (live[p] && a.anc) (a.anc + ibase)[32u * p] = static_cast<int32_t>(k[p]);
   if constexpr (GATHER == kGatherSoa) {
     for (int d = 0; d < a.dim; ++d) {
       const float* src = a.x_in + static_cast<int64_t>(d) * a.ld;
@@ -113,7 +126,7 @@ __device__ __forceinline__ void finish_batch(const Problem& a, uint32_t ibase,
       for (int p = 0; p < P; ++p) v[p] = live[p] ? __ldg(src + k[p]) : 0.0f;
 #pragma unroll
       for (int p = 0; p < P; ++p)
-        if (live[p]) dst[ibase + 32u * p] = v[p];
+        if (live[p]) (dst + ibase)[32u * p] = v[p];
     }
   } else if constexpr (GATHER == kGatherAos4) {
     const float4* src = reinterpret_cast<const float4*>(a.x_in);
@@ -124,36 +137,46 @@ __device__ __forceinline__ void finish_batch(const Problem& a, uint32_t ibase,
       v[p] = live[p] ? __ldg(src + k[p]) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int p = 0; p < P; ++p)
-      if (live[p]) dst[ibase + 32u * p] = v[p];
+      if (live[p]) (dst + ibase)[32u * p] = v[p];
   }
+}
+
+// Column of one Megopolis iteration for a lane: x0 = base + (lane + o) mod 32,
+// where (base, o) is the iteration's table entry.  Segment p of the batch
+// reads index x0 + 32 p, reduced modulo n (wrap_index) where it may run past
+// n.
+__device__ __forceinline__ uint32_t mego_column(int2 e, uint32_t lane) {
+  return static_cast<uint32_t>(e.x) + ((lane + static_cast<uint32_t>(e.y)) & 31u);
+}
+
+__device__ __forceinline__ uint32_t wrap_index(uint32_t j, uint32_t n) {
+  if (j >= n) j -= n;
+  if (j >= n) j %= n;
+  return j;
 }
 
 // Loads of one Megopolis iteration for the P segments of a batch when the
 // partitions may run past n: each index is reduced modulo n.
 template <int P, bool SMEM>
-__device__ __forceinline__ void mego_wrapped_loads(const Problem& a, int2 e,
-                                                   uint32_t lane, float (&wj)[P]) {
-  const uint32_t n = a.n;
-  const uint32_t x0 = static_cast<uint32_t>(e.x) + ((lane + static_cast<uint32_t>(e.y)) & 31u);
+__device__ __forceinline__ void mego_wrapped_loads(const Problem& a, uint32_t x0,
+                                                   float (&wj)[P]) {
 #pragma unroll
-  for (int p = 0; p < P; ++p) {
-    uint32_t j = x0 + 32u * p;
-    if (j >= n) j -= n;
-    if (j >= n) j %= n;
-    wj[p] = ldw<SMEM>(a.w, j);
-  }
+  for (int p = 0; p < P; ++p) wj[p] = ldw<SMEM>(a.w, wrap_index(x0 + 32u * p, a.n));
 }
 
 // ---------------------------------------------------------------------------
 // Megopolis (Algorithm 5).  Iteration b, particle i = 32 s + lane:
 //   j = (32 s + o_al + (lane + o) mod 32) mod n,  o_al = o - o mod 32.
 // The warp reads one aligned 32-weight partition per segment and iteration.
-// Every 32 iterations each lane draws the offset of one iteration and stores
-// (wrapped base of the warp's first segment, offset) in the warp's table;
-// a ballot marks the iterations whose P partitions do not run past n, so the
-// common case loads at x0 + 32 p with immediate offsets.  Chains record the
-// iteration b of their last acceptance (a uniform value) and the ancestor
-// index is rebuilt from o^(b) once, after the last iteration.
+// Iterations run in groups of five (one Philox call per particle and group).
+// The warp's table holds 32 consecutive offsets: each lane draws the offset of
+// one iteration and stores (wrapped base of the warp's first segment, offset);
+// the table is refilled every six groups (30 iterations), so a group never
+// straddles two tables.  A ballot marks the iterations whose P partitions do
+// not run past n, so the common case loads at x0 + 32 p with immediate
+// offsets.  A chain keeps the column x0 of its last accepted proposal (its
+// index less 32 p, before the reduction modulo n); the ancestor is that
+// column plus 32 p, reduced once after the last iteration.
 template <int P, bool SMEM, int GATHER>
 __device__ __forceinline__ void megopolis_batch(const Problem& a, const RoundKeys& K, int B,
                                                 uint32_t s0, uint32_t seg_hi,
@@ -161,7 +184,7 @@ __device__ __forceinline__ void megopolis_batch(const Problem& a, const RoundKey
   const uint32_t n = a.n;
   const uint32_t ibase = s0 * 32u + lane;
   float wk[P];
-  int kb[P];
+  uint32_t kx[P];  // column of the current state: ancestor = (kx + 32 p) mod n
   bool live[P];
   PhiloxLane ph[P];
 #pragma unroll
@@ -169,12 +192,16 @@ __device__ __forceinline__ void megopolis_batch(const Problem& a, const RoundKey
     const uint32_t i = ibase + 32u * p;
     live[p] = (s0 + p < seg_hi) && (i < n);
     wk[p] = ldw<SMEM>(a.w, i < n ? i : n - 1u);
-    kb[p] = -1;
+    kx[p] = ibase;
     ph[p].init(i, kTagMegoU, K, a.S);
   }
+  constexpr int U = kMegoPerCall;
+  constexpr uint32_t kFull = (1u << U) - 1u;
   uint32_t fast_mask = 0u;
-  for (int b0 = 0; b0 < B; b0 += 4) {
-    if ((b0 & 31) == 0) {
+  int t0 = 32;  // position of iteration b0 in the table; 32 forces a refill
+  uint32_t g = 0u;
+  for (int b0 = 0; b0 < B; b0 += U, ++g, t0 += U) {
+    if (t0 + U > 32) {
       const uint32_t o = mego_offset(K, a.S, static_cast<uint32_t>(b0) + lane, n);
       uint32_t base = s0 * 32u + (o & ~31u);
       base = base >= n ? base - n : base;
@@ -182,55 +209,58 @@ __device__ __forceinline__ void megopolis_batch(const Problem& a, const RoundKey
       __syncwarp();
       win[lane] = make_int2(static_cast<int>(base), static_cast<int>(o));
       __syncwarp();
+      t0 = 0;
     }
-    const int t0 = b0 & 31;
     uint32_t mh, ml;
-    PhiloxLane::group(static_cast<uint32_t>(b0) >> 2, a.S, mh, ml);
-    float wj[4][P];
-    if (B - b0 >= 4) {
-      // Four full iterations.
-      if (((fast_mask >> t0) & 0xFu) == 0xFu) {
+    PhiloxLane::group(g, a.S, mh, ml);
+    float wj[U][P];
+    uint32_t x0[U];
+    if (B - b0 >= U) {
+      // A full group of five iterations.
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int2 e = win[t0 + q];
-          const uint32_t x0 = static_cast<uint32_t>(e.x) +
-                              ((lane + static_cast<uint32_t>(e.y)) & 31u);
+      for (int q = 0; q < U; ++q) x0[q] = mego_column(win[t0 + q], lane);
+      if (((fast_mask >> t0) & kFull) == kFull) {
 #pragma unroll
-          for (int p = 0; p < P; ++p) wj[q][p] = ldw<SMEM>(a.w, x0 + 32u * p);
-        }
+        for (int q = 0; q < U; ++q)
+#pragma unroll
+          for (int p = 0; p < P; ++p) wj[q][p] = ldw_at<SMEM>(a.w, x0[q], 32u * p);
       } else {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) mego_wrapped_loads<P, SMEM>(a, win[t0 + q], lane, wj[q]);
+        for (int q = 0; q < U; ++q) mego_wrapped_loads<P, SMEM>(a, x0[q], wj[q]);
       }
       uint4 r[P];
 #pragma unroll
       for (int p = 0; p < P; ++p) r[p] = ph[p].gen(mh, ml, K);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 0; q < U; ++q) {
 #pragma unroll
         for (int p = 0; p < P; ++p) {
-          const bool acc = accept(u_of(word_of(r[p], q)), wk[p], wj[q][p]);
+          const bool acc = accept(u_of(mego_word(r[p], q)), wk[p], wj[q][p]);
           wk[p] = acc ? wj[q][p] : wk[p];
-          kb[p] = acc ? b0 + q : kb[p];
+          kx[p] = acc ? x0[q] : kx[p];
         }
       }
     } else {
-      // Tail: 1..3 iterations.
+      // Tail: 1..4 iterations (words 0..3 of the call).
       const int nb = B - b0;
 #pragma unroll
-      for (int q = 0; q < 3; ++q)
-        if (q < nb) mego_wrapped_loads<P, SMEM>(a, win[t0 + q], lane, wj[q]);
+      for (int q = 0; q < U - 1; ++q) {
+        if (q < nb) {
+          x0[q] = mego_column(win[t0 + q], lane);
+          mego_wrapped_loads<P, SMEM>(a, x0[q], wj[q]);
+        }
+      }
       uint4 r[P];
 #pragma unroll
       for (int p = 0; p < P; ++p) r[p] = ph[p].gen(mh, ml, K);
 #pragma unroll
-      for (int q = 0; q < 3; ++q) {
+      for (int q = 0; q < U - 1; ++q) {
         if (q < nb) {
 #pragma unroll
           for (int p = 0; p < P; ++p) {
             const bool acc = accept(u_of(word_of(r[p], q)), wk[p], wj[q][p]);
             wk[p] = acc ? wj[q][p] : wk[p];
-            kb[p] = acc ? b0 + q : kb[p];
+            kx[p] = acc ? x0[q] : kx[p];
           }
         }
       }
@@ -238,16 +268,7 @@ __device__ __forceinline__ void megopolis_batch(const Problem& a, const RoundKey
   }
   uint32_t k[P];
 #pragma unroll
-  for (int p = 0; p < P; ++p) {
-    k[p] = ibase + 32u * p;
-    if (kb[p] >= 0) {
-      const uint32_t o = mego_offset(K, a.S, static_cast<uint32_t>(kb[p]), n);
-      uint32_t x = (s0 + p) * 32u + (o & ~31u) + ((lane + o) & 31u);
-      if (x >= n) x -= n;
-      if (x >= n) x %= n;
-      k[p] = x;
-    }
-  }
+  for (int p = 0; p < P; ++p) k[p] = wrap_index(kx[p] + 32u * p, n);
   finish_batch<P, GATHER>(a, ibase, k, live);
 }
 

@@ -93,8 +93,47 @@ def test_megopolis_u_uniform():
     assert us.min() > 0.0 and us.max() <= 1.0
     ks = stats.kstest(us, "uniform")
     assert ks.pvalue > 1e-3
-    # the four words of one call are used by four consecutive iterations
+    # the five uniforms of one call are used by five consecutive iterations
     assert len(set(us.tolist())) > 0.99 * us.size
+
+
+def test_megopolis_u_word_layout():
+    """Iteration b of particle i reads call (i, b // 5, sid, 2): words 0..3
+    for b mod 5 < 4, the top bytes of words 0..2 for b mod 5 = 4."""
+    seed = 0x0123456789ABCDEF
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for sid in (0, 7):
+        for i in (0, 1, 31, 1000, 2**30 - 1):
+            for b in range(12):
+                x = [int(v) for v in oracle.philox4x32_10([i, b // 5, sid, 2], key)]
+                q = b % 5
+                word = x[q] if q < 4 else (x[0] >> 24) | (x[1] >> 24) << 8 | (x[2] >> 24) << 16
+                assert oracle.megopolis_u(seed, sid, i, b) == np.float32(oracle.u_from_word(word))
+
+
+def test_megopolis_five_uniforms_independent():
+    """The five uniforms of one Philox call come from disjoint bits: each is
+    uniform on the 2^-23 grid and they are uncorrelated with one another
+    (a fifth word that reused bits of the first three would correlate)."""
+    m = 4000
+    u = np.array([[oracle.megopolis_u(3, 1, i, 5 * g + q) for q in range(5)]
+                  for i in range(m // 4) for g in range(4)], dtype=np.float64)
+    for q in range(5):
+        assert stats.kstest(u[:, q], "uniform").pvalue > 1e-3
+        grid = u[:, q] * 2.0 ** 23
+        assert np.all(grid == np.round(grid))
+    c = np.corrcoef(u.T)
+    off = c[~np.eye(5, dtype=bool)]
+    # sd of a sample correlation of independent uniforms is 1/sqrt(m)
+    assert np.abs(off).max() < 5.0 / np.sqrt(m)
+    # Bit by bit: the 23 random bits behind each uniform (recovered exactly
+    # from u) agree with any bit of another uniform of the call about half
+    # the time; a shared bit would agree always (or never).
+    bits = (2 ** 23 - np.round(u * 2.0 ** 23).astype(np.int64)) & 0x7FFFFF
+    planes = ((bits[:, :, None] >> np.arange(23)) & 1).astype(np.float64)  # [m, 5, 23]
+    for q in range(4):
+        agree = (planes[:, 4, :, None] == planes[:, q, None, :]).mean(axis=0)  # [23, 23]
+        assert np.abs(agree - 0.5).max() < 0.1, q
 
 
 @pytest.mark.parametrize("n", [4, 37, 1000, 4096])
