@@ -47,6 +47,16 @@ SEED = 1
 # particle and the stream, and one call serves five proposals.
 MULS_PER_PROPOSAL = 15.0 / 5.0
 FLUSH_BYTES = 256 << 20
+# Before a run of event-timed launches the stream gets a sleep kernel of this
+# many microseconds, so the host has enqueued the whole run before the GPU
+# reaches it: the events then bracket GPU work only, not Python launch time.
+HOLD_US_PER_LAUNCH = 60
+
+
+def _hold(torch, launches):
+    """Keep the GPU busy (outside any timed interval) for long enough that the
+    host can enqueue `launches` library calls behind it."""
+    torch.cuda._sleep(int(HOLD_US_PER_LAUNCH * launches * 2100))
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "batch_resample_sweep5_n2p20.md")
 KERNEL_SOURCES = ("resample_kernels.cuh", "device_common.cuh", "batch.cu")
 
@@ -330,6 +340,7 @@ def _sir_leg(args, mego, synthetic, torch, dev):
                                      dtype=torch.uint8, device=dev)
                     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)]
                           for _ in range(T)]
+                    _hold(torch, 3 * T)
                     for t in range(1, T + 1):
                         e = ev[t - 1]
                         e[0].record(stream)
@@ -380,6 +391,7 @@ def _sweep_leg(args, mego, synthetic, torch, dev):
                 ts = []
                 for _ in range(args.sweep_reps):
                     flush.zero_()
+                    _hold(torch, 1)
                     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                     a.record(stream)
                     mego.mego_resample_gather(w, B, None, SEED, 0, variant, anc=anc, cfg=cfg,
@@ -490,6 +502,7 @@ def run_gpu(args):
                                                  else "metropolis"))
         for s in range(steps):
             flush.zero_()
+            _hold(torch, 3 * len(YS))
             step(variant, evs[s])
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize(dev)
@@ -626,6 +639,7 @@ def run_gpu(args):
     fused = []
     for s in range(args.warmup + max(3, args.steps // 4)):
         flush.zero_()
+        _hold(torch, 3)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         mego.mego_likelihood_B(x[0], 2.0, EPS, w=wf, B_dev=B_dev[0], status=st_dev[0],

@@ -133,8 +133,20 @@ __global__ void __launch_bounds__(kBoundThreads) batch_partials_kernel(const __g
   const float* w = F[f].w;
   const uint32_t lo = (chunk - cp[f]) * kChunk;
   const uint32_t hi = min(n, lo + kChunk);
+  // All of a thread's weights are loaded before the (sequential) compensated
+  // sum starts, so the chunk costs one memory latency; the sum still runs in
+  // index order.
+  constexpr int kPer = static_cast<int>(kChunk) / kBoundThreads;
+  float v[kPer];
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    const uint32_t i = lo + threadIdx.x + static_cast<uint32_t>(k) * kBoundThreads;
+    v[k] = i < hi ? __ldg(w + i) : 0.0f;
+  }
   BAcc acc;
-  for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) acc.add(__ldg(w + i));
+#pragma unroll
+  for (int k = 0; k < kPer; ++k)
+    if (lo + threadIdx.x + static_cast<uint32_t>(k) * kBoundThreads < hi) acc.add(v[k]);
   // Fixed-order tree: warp shuffles, then warp 0 over the warp results.
   double sum = static_cast<double>(acc.s) + static_cast<double>(acc.c);
   float mx = acc.mx;
@@ -183,11 +195,21 @@ __global__ void __launch_bounds__(256) batch_finalize_kernel(const __grid_consta
   double sum = 0.0;
   float mx = 0.0f;
   int bad = 0;
-  for (uint32_t c = cp[f] + lane; c < cp[f + 1]; c += 32u) {
-    const Partial p = parts[c];
-    sum += p.sum;
-    mx = fmaxf(mx, p.mx);
-    bad |= p.bad;
+  // Loads go out eight at a time, ahead of the (order-dependent) sums.
+  const uint32_t c_end = cp[f + 1];
+  for (uint32_t c0 = cp[f] + lane; c0 < c_end; c0 += 8u * 32u) {
+    Partial p[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (c0 + 32u * k < c_end) p[k] = parts[c0 + 32u * k];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (c0 + 32u * k < c_end) {
+        sum += p[k].sum;
+        mx = fmaxf(mx, p[k].mx);
+        bad |= p[k].bad;
+      }
+    }
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {

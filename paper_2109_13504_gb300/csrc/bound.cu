@@ -107,26 +107,29 @@ partials_kernel(const float* __restrict__ src, uint32_t n, float y,
     const uint32_t n4 = n / 4u;
     const float4* s4 = reinterpret_cast<const float4*>(src);
     float4* w4 = reinterpret_cast<float4*>(w_out);
-    // Two independent loads in flight per thread before any accumulation.
+    // Four independent 16-byte loads in flight per thread before any
+    // accumulation (one DRAM latency per four vectors); the values are still
+    // added in index order t0, t0 + stride, t0 + 2 stride, ...
     uint32_t t = t0;
-    for (; t + stride < n4; t += 2u * stride) {
-      const float4 v0 = weight4<LIKELIHOOD>(__ldg(s4 + t), y, w4, t);
-      const float4 v1 = weight4<LIKELIHOOD>(__ldg(s4 + t + stride), y, w4, t + stride);
-      a.add(v0.x);
-      a.add(v0.y);
-      a.add(v0.z);
-      a.add(v0.w);
-      a.add(v1.x);
-      a.add(v1.y);
-      a.add(v1.z);
-      a.add(v1.w);
+    for (; t + 3u * stride < n4; t += 4u * stride) {
+      float4 v[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) v[k] = __ldg(s4 + t + k * stride);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float4 x = weight4<LIKELIHOOD>(v[k], y, w4, t + k * stride);
+        a.add(x.x);
+        a.add(x.y);
+        a.add(x.z);
+        a.add(x.w);
+      }
     }
-    if (t < n4) {
-      const float4 v0 = weight4<LIKELIHOOD>(__ldg(s4 + t), y, w4, t);
-      a.add(v0.x);
-      a.add(v0.y);
-      a.add(v0.z);
-      a.add(v0.w);
+    for (; t < n4; t += stride) {
+      const float4 x = weight4<LIKELIHOOD>(__ldg(s4 + t), y, w4, t);
+      a.add(x.x);
+      a.add(x.y);
+      a.add(x.z);
+      a.add(x.w);
     }
     tail = n4 * 4u;
   }
@@ -149,10 +152,16 @@ finalize_kernel(const Partial* __restrict__ parts, int nparts, uint32_t n, doubl
                 double* __restrict__ d_q) {
   // One warp: each lane folds its strided partials in index order, then a
   // fixed shuffle tree combines the lanes.
+  // Loads go out eight at a time, ahead of the (order-dependent) merges.
   Acc a{0.0f, 0, 0.0};
-  for (int t = threadIdx.x; t < nparts; t += 32) {
-    const Partial p = parts[t];
-    acc_merge(a, Acc{p.mx, p.bad, p.sum});
+  for (int t0 = threadIdx.x; t0 < nparts; t0 += 8 * 32) {
+    Partial p[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (t0 + 32 * k < nparts) p[k] = parts[t0 + 32 * k];
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (t0 + 32 * k < nparts) acc_merge(a, Acc{p[k].mx, p[k].bad, p[k].sum});
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {

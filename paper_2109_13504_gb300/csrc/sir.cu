@@ -44,14 +44,26 @@ __global__ void __launch_bounds__(kThreads)
 mean_partials_kernel(const float* __restrict__ x, uint32_t n, double* __restrict__ parts) {
   double s = 0.0;
   const uint32_t stride = gridDim.x * blockDim.x;
-  // Compensated float accumulation per thread; one conversion to double.
+  // Compensated float accumulation per thread, in index order; one
+  // conversion to double.  Sixteen loads are issued before they are summed,
+  // so a pass costs one memory latency per sixteen values.
+  constexpr int kPer = 16;
   float hi = 0.0f, lo = 0.0f;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const float v = __ldg(x + i);
-    const float t = __fadd_rn(hi, v);
-    lo = __fadd_rn(lo, fabsf(hi) >= fabsf(v) ? __fadd_rn(__fsub_rn(hi, t), v)
-                                              : __fadd_rn(__fsub_rn(v, t), hi));
-    hi = t;
+  for (uint32_t base = blockIdx.x * blockDim.x + threadIdx.x; base < n; base += kPer * stride) {
+    float v[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const uint32_t i = base + static_cast<uint32_t>(k) * stride;
+      v[k] = i < n ? __ldg(x + i) : 0.0f;
+    }
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      if (base + static_cast<uint32_t>(k) * stride >= n) break;
+      const float t = __fadd_rn(hi, v[k]);
+      lo = __fadd_rn(lo, fabsf(hi) >= fabsf(v[k]) ? __fadd_rn(__fsub_rn(hi, t), v[k])
+                                                  : __fadd_rn(__fsub_rn(v[k], t), hi));
+      hi = t;
+    }
   }
   s = static_cast<double>(hi) + static_cast<double>(lo);
 #pragma unroll
@@ -68,8 +80,16 @@ mean_partials_kernel(const float* __restrict__ x, uint32_t n, double* __restrict
 
 __global__ void mean_finalize_kernel(const double* __restrict__ parts, int nparts, uint32_t n,
                                      double* __restrict__ out) {
+  // Each lane folds its strided partials in index order, eight loads ahead.
   double s = 0.0;
-  for (int k = threadIdx.x; k < nparts; k += 32) s += parts[k];
+  for (int k0 = threadIdx.x; k0 < nparts; k0 += 8 * 32) {
+    double v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = k0 + 32 * j < nparts ? parts[k0 + 32 * j] : 0.0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (k0 + 32 * j < nparts) s += v[j];
+  }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xFFFFFFFFu, s, off);
   if (threadIdx.x == 0) *out = s / static_cast<double>(n);
@@ -89,7 +109,9 @@ extern "C" {
 mego_status mego_sir_predict_update(const float* d_x, const float* d_v, int32_t n, float drift,
                                     float z, float* d_x_pred, float* d_w, void* stream) {
   if (!d_x || !d_v || !d_x_pred || !d_w || n < 1 || n > MEGO_N_MAX) return MEGO_EINVAL;
-  const int grid = grid_for(static_cast<uint32_t>(n), 152 * 8);
+  // One particle per thread: every load of the launch is in flight at once
+  // (a grid-stride loop would wait one memory latency per element).
+  const int grid = static_cast<int>((static_cast<uint32_t>(n) + kThreads - 1u) / kThreads);
   predict_update_kernel<<<grid, kThreads, 0, static_cast<cudaStream_t>(stream)>>>(
       d_x, d_v, static_cast<uint32_t>(n), drift, z, d_x_pred, d_w);
   if (cudaGetLastError() != cudaSuccess) return MEGO_ECUDA;
