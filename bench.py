@@ -652,21 +652,27 @@ def run_gpu(args):
             fused.append(a.elapsed_time(b))
 
     # End to end through the public host-buffer API: every step submits the
-    # five vectors (page-locked host memory) to the serving loop, which
-    # uploads them, runs one batched launch, copies the ancestors back, and
-    # the step ends when all five are on the host.
+    # five vectors (page-locked host memory) to the serving loop, one stream
+    # per request, which uploads each, runs its bound and resample, copies the
+    # ancestors back; the step ends when all five are on the host.  The client
+    # submits longest first by the B each vector had at its previous step (the
+    # completions report it), so the long chain starts first and the short
+    # ones, their copies included, overlap with it.
     h_w = [torch.from_numpy(synthetic.gaussian_weights(N, y, SEED + y)).pin_memory() for y in YS]
     h_anc = [torch.empty(N, dtype=torch.int32).pin_memory() for _ in YS]
-    server = mego.Server(arena_bytes=256 << 20, seed=SEED, max_batch=len(YS), streams=2,
+    server = mego.Server(arena_bytes=512 << 20, seed=SEED, max_batch=1, streams=len(YS),
                          with_state=False, device=dev)
     e2e_steps = max(3, args.steps // 4)
+    last_B = [0] * len(YS)
     for s_ in range(args.warmup + e2e_steps):
         if s_ == args.warmup:
             t0 = time.perf_counter()
-        for t in range(len(YS)):
+        order = sorted(range(len(YS)), key=lambda t: -last_B[t])
+        for t in order:
             server.submit(s_ * len(YS) + t, h_w[t], None, h_anc[t], None)
         server.drain(60.0)
-        server.poll()
+        for c in server.poll():
+            last_B[int(c[0]) % len(YS)] = int(c[4])
     e2e_s = time.perf_counter() - t0
     server.close()
     e2e_value = N * len(YS) * e2e_steps / e2e_s
@@ -755,9 +761,10 @@ def run_gpu(args):
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": 4 * N * len(YS),
-                "d2h_bytes_per_step": 4 * N * len(YS),
-                "path": "mego_server_submit x5 + drain per step (host buffers, one batched "
-                        "launch, uploads and downloads inside the timed region)"},
+                "d2h_bytes_per_step": 4 * N * len(YS) + 4 * len(YS),
+                "path": "mego_server_submit x5 (longest first by the previous step's B) + "
+                        "drain per step, one stream per request; host buffers, uploads and "
+                        "downloads (ancestors and B) inside the timed region"},
         "gpu_launches": launches,
         "cpu_baseline": cpu,
     }

@@ -42,7 +42,7 @@
 extern "C" {
 #endif
 
-#define MEGO_ABI_VERSION 1
+#define MEGO_ABI_VERSION 2
 #define MEGO_N_MAX (1 << 30)
 #define MEGO_B_MAX (1 << 24)
 
@@ -301,6 +301,10 @@ typedef struct mego_completion {
   int32_t status;       /* MEGO_OK, or the error that failed the batch        */
   int32_t n;
   int64_t latency_ns;   /* from submission to the results being on the host   */
+  int32_t B;            /* iterations the bound gave this request (Eq. 3), or
+                           -1 where it failed; a client can order its next
+                           submissions by it (longest first)                  */
+  int32_t reserved;
 } mego_completion;
 
 typedef struct mego_server_cfg {

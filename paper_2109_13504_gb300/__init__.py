@@ -82,7 +82,8 @@ class Request(ctypes.Structure):
 
 class Completion(ctypes.Structure):
     _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int32), ("n", ctypes.c_int32),
-                ("latency_ns", ctypes.c_int64)]
+                ("latency_ns", ctypes.c_int64), ("B", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class ServerCfg(ctypes.Structure):
@@ -579,6 +580,7 @@ class Server:
         _check(lib.mego_server_create(ctypes.byref(cfg), ctypes.byref(self._h)),
                "mego_server_create")
         self._keep = {}
+        self._poll_buf = {}
 
     def _req(self, rid, w, x=None, anc=None, x_out=None):
         return Request(int(rid), _host_ptr(w, torch.float32, "w"),
@@ -591,9 +593,12 @@ class Server:
         _check(_load().mego_server_submit(self._h, ctypes.byref(r)), "mego_server_submit")
 
     def poll(self, max_out: int = 4096):
-        buf = (Completion * max_out)()
+        """Completed requests as (id, status, n, latency_ns, B) tuples."""
+        buf = self._poll_buf.get(max_out)
+        if buf is None:
+            buf = self._poll_buf[max_out] = (Completion * max_out)()
         k = _load().mego_server_poll(self._h, buf, int(max_out))
-        out = [(c.id, c.status, c.n, c.latency_ns) for c in buf[:k]]
+        out = [(c.id, c.status, c.n, c.latency_ns, c.B) for c in buf[:k]]
         for c in out:
             self._keep.pop(int(c[0]), None)
         return out

@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/megopolis.h"
+#include "batch_plan.h"
 #include "bound.cuh"
 #include "resample_kernels.cuh"
 
@@ -417,7 +418,20 @@ size_t mego_batch_plan_bytes(const mego_filter* h_filters, int32_t count) {
 mego_status mego_batch_plan(const mego_filter* h_filters, int32_t count, int variant,
                             int layout, uint64_t seed, void* d_plan, size_t plan_bytes,
                             mego_batch* out, void* stream) {
-  using namespace mego;
+  // Pageable staging: the copy has read it by the time cudaMemcpyAsync returns.
+  std::vector<unsigned char> host;
+  return mego::batch_plan_staged(h_filters, count, variant, layout, seed, d_plan, plan_bytes,
+                                 &host, nullptr, 0, out, stream);
+}
+
+}  // extern "C"
+
+namespace mego {
+
+mego_status batch_plan_staged(const mego_filter* h_filters, int32_t count, int variant,
+                              int layout, uint64_t seed, void* d_plan, size_t plan_bytes,
+                              std::vector<unsigned char>* pageable, void* staging,
+                              size_t staging_bytes, mego_batch* out, void* stream) {
   if (!h_filters || count < 1 || !d_plan || !out) return MEGO_EINVAL;
   if (variant != MEGO_MEGOPOLIS && variant != MEGO_METROPOLIS) return MEGO_EINVAL;
   if (layout != MEGO_LAYOUT_SOA && layout != MEGO_LAYOUT_AOS4) return MEGO_EINVAL;
@@ -445,16 +459,24 @@ mego_status mego_batch_plan(const mego_filter* h_filters, int32_t count, int var
     }
   }
   if (has_state && no_state) return MEGO_EINVAL;  // one gather layout per batch
-  std::vector<unsigned char> host(L.parts, 0);
+  unsigned char* host = nullptr;
+  if (pageable) {
+    pageable->assign(L.parts, 0);
+    host = pageable->data();
+  } else {
+    if (!staging || staging_bytes < L.parts) return MEGO_ENOMEM;
+    host = static_cast<unsigned char*>(staging);
+    std::memset(host, 0, L.parts);
+  }
   PlanHeader hdr{};
   hdr.count = static_cast<uint32_t>(count);
   hdr.total_items = static_cast<uint32_t>(items);
   hdr.total_chunks = static_cast<uint32_t>(chunks);
-  std::memcpy(host.data(), &hdr, sizeof hdr);
-  FilterDev* F = reinterpret_cast<FilterDev*>(host.data() + L.filters);
-  uint32_t* ip = reinterpret_cast<uint32_t*>(host.data() + L.item_prefix);
-  uint32_t* cp = reinterpret_cast<uint32_t*>(host.data() + L.chunk_prefix);
-  int32_t* Bv = reinterpret_cast<int32_t*>(host.data() + L.B);
+  std::memcpy(host, &hdr, sizeof hdr);
+  FilterDev* F = reinterpret_cast<FilterDev*>(host + L.filters);
+  uint32_t* ip = reinterpret_cast<uint32_t*>(host + L.item_prefix);
+  uint32_t* cp = reinterpret_cast<uint32_t*>(host + L.chunk_prefix);
+  int32_t* Bv = reinterpret_cast<int32_t*>(host + L.B);
   uint64_t it = 0, ch = 0;
   for (int32_t f = 0; f < count; ++f) {
     const mego_filter& d = h_filters[f];
@@ -469,10 +491,9 @@ mego_status mego_batch_plan(const mego_filter* h_filters, int32_t count, int var
   }
   ip[count] = static_cast<uint32_t>(it);
   cp[count] = static_cast<uint32_t>(ch);
-  if (cudaMemcpyAsync(d_plan, host.data(), host.size(), cudaMemcpyHostToDevice,
+  if (cudaMemcpyAsync(d_plan, host, L.parts, cudaMemcpyHostToDevice,
                       static_cast<cudaStream_t>(stream)) != cudaSuccess)
     return MEGO_ECUDA;
-  // The copy reads `host` before cudaMemcpyAsync returns (pageable source).
   std::memset(out, 0, sizeof *out);
   out->d_plan = d_plan;
   out->plan_bytes = L.total;
@@ -501,6 +522,10 @@ mego_status mego_batch_plan(const mego_filter* h_filters, int32_t count, int var
   out->grid = grid;
   return MEGO_OK;
 }
+
+}  // namespace mego
+
+extern "C" {
 
 mego_status mego_batch_bound(const mego_batch* b, double eps, int32_t b_max, void* stream) {
   using namespace mego;

@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/megopolis.h"
+#include "batch_plan.h"
 
 namespace {
 
@@ -120,6 +121,7 @@ struct mego_server {
   Arena arena;
   std::vector<cudaStream_t> streams;
   std::vector<bool> stream_busy;
+  std::vector<void*> staging;     // page-locked plan staging, one per stream
   std::mutex mu;
   std::condition_variable cv;
   std::deque<Req> queue;          // submitted, not admitted
@@ -127,6 +129,7 @@ struct mego_server {
   std::vector<InFlight> inflight;
   std::vector<mego_completion> done;
   std::atomic<bool> stop{false};
+  int launching = 0;              // batches taken from `admitted`, not yet in flight
   std::thread worker;
   size_t plan_slice = 0;          // bytes of plan space per stream (arena front)
   size_t admitted_plan = 0;       // plan bytes the admitted set will need
@@ -136,11 +139,17 @@ struct mego_server {
   size_t peak_used = 0;
 
   void run();
-  bool launch_batch(std::vector<Req>& reqs, int si);
+  bool launch_batch(const std::vector<Req>& reqs, int si, InFlight* f);
+  bool busy() const {
+    return !(queue.empty() && admitted.empty() && inflight.empty() && launching == 0);
+  }
   void finish(InFlight& f);
 };
 
-bool mego_server::launch_batch(std::vector<Req>& reqs, int si) {
+// Queues one batch on stream si: uploads, plan, bound, resample, downloads and
+// the completion event.  Touches no shared server state, so the worker runs
+// it without the lock (stream si and its staging buffer are reserved).
+bool mego_server::launch_batch(const std::vector<Req>& reqs, int si, InFlight* f) {
   cudaStream_t st = streams[si];
   char* base = static_cast<char*>(cfg.d_arena);
   std::vector<mego_filter> filters(reqs.size());
@@ -163,17 +172,18 @@ bool mego_server::launch_batch(std::vector<Req>& reqs, int si) {
                              q.r.n, -1, static_cast<uint32_t>(q.r.id), state ? 4 : 0};
   }
   // One gather layout per batch: all with state or all without.
-  InFlight f;
-  f.plan_bytes = mego_batch_plan_bytes(filters.data(), static_cast<int32_t>(filters.size()));
-  if (f.plan_bytes == 0 || f.plan_bytes > plan_slice) return false;
-  f.plan_off = static_cast<size_t>(si) * plan_slice;  // this stream's plan slice
-  bool ok = mego_batch_plan(filters.data(), static_cast<int32_t>(filters.size()), cfg.variant,
-                            MEGO_LAYOUT_AOS4, cfg.seed, base + f.plan_off, f.plan_bytes,
-                            &f.batch, st) == MEGO_OK;
+  f->plan_bytes = mego_batch_plan_bytes(filters.data(), static_cast<int32_t>(filters.size()));
+  if (f->plan_bytes == 0 || f->plan_bytes > plan_slice) return false;
+  f->plan_off = static_cast<size_t>(si) * plan_slice;  // this stream's plan slice
+  bool ok = mego::batch_plan_staged(filters.data(), static_cast<int32_t>(filters.size()),
+                                    cfg.variant, MEGO_LAYOUT_AOS4, cfg.seed, base + f->plan_off,
+                                    f->plan_bytes, nullptr, staging[si], plan_slice, &f->batch,
+                                    st) == MEGO_OK;
   if (ok && cfg.threads > 0)
-    ok = mego_batch_set_shape(&f.batch, cfg.threads, cfg.ppt > 0 ? cfg.ppt : 2) == MEGO_OK;
-  ok = ok && mego_batch_bound(&f.batch, cfg.eps, MEGO_B_MAX, st) == MEGO_OK;
-  ok = ok && mego_batch_resample(&f.batch, st) == MEGO_OK;
+    ok = mego_batch_set_shape(&f->batch, cfg.threads,
+                              cfg.ppt > 0 ? cfg.ppt : f->batch.cfg.ppt) == MEGO_OK;
+  ok = ok && mego_batch_bound(&f->batch, cfg.eps, MEGO_B_MAX, st) == MEGO_OK;
+  ok = ok && mego_batch_resample(&f->batch, st) == MEGO_OK;
   for (size_t k = 0; ok && k < reqs.size(); ++k) {
     const Req& q = reqs[k];
     if (q.r.h_anc)
@@ -183,9 +193,13 @@ bool mego_server::launch_batch(std::vector<Req>& reqs, int si) {
       ok = cudaMemcpyAsync(q.r.h_x_out, filters[k].x_out, 16 * static_cast<size_t>(q.r.n),
                            cudaMemcpyDeviceToHost, st) == cudaSuccess;
   }
-  ok = ok && cudaEventCreateWithFlags(&f.done, cudaEventDisableTiming) == cudaSuccess;
-  if (ok && cudaEventRecord(f.done, st) != cudaSuccess) {
-    cudaEventDestroy(f.done);
+  // Each request's B comes back into the stream's staging buffer (its plan
+  // copy ran earlier on the same stream); finish() reads it.
+  ok = ok && cudaMemcpyAsync(staging[si], f->batch.d_B, sizeof(int32_t) * reqs.size(),
+                             cudaMemcpyDeviceToHost, st) == cudaSuccess;
+  ok = ok && cudaEventCreateWithFlags(&f->done, cudaEventDisableTiming) == cudaSuccess;
+  if (ok && cudaEventRecord(f->done, st) != cudaSuccess) {
+    cudaEventDestroy(f->done);
     ok = false;
   }
   if (!ok) {
@@ -193,23 +207,21 @@ bool mego_server::launch_batch(std::vector<Req>& reqs, int si) {
     cudaStreamSynchronize(st);
     return false;
   }
-  f.reqs.swap(reqs);
-  f.stream = si;
-  stream_busy[si] = true;
-  batches += 1;
-  if (f.reqs.size() > max_batch) max_batch = f.reqs.size();
-  inflight.push_back(std::move(f));
+  f->stream = si;
   return true;
 }
 
 void mego_server::finish(InFlight& f) {
   const int64_t t = now_ns();
-  for (const Req& q : f.reqs) {
+  const int32_t* Bs = static_cast<const int32_t*>(staging[f.stream]);
+  for (size_t k = 0; k < f.reqs.size(); ++k) {
+    const Req& q = f.reqs[k];
     mego_completion c{};
     c.id = q.r.id;
     c.status = MEGO_OK;
     c.latency_ns = t - q.t_submit;
     c.n = q.r.n;
+    c.B = Bs[k];
     done.push_back(c);
     arena.release(q.off, q.bytes);
   }
@@ -258,13 +270,29 @@ void mego_server::run() {
         std::vector<Req> reqs;
         reqs.swap(admitted);
         admitted_plan = 0;
-        if (!launch_batch(reqs, si)) {
+        // Launch without the lock, so submissions and polls are not held up
+        // by the host side of the launch.
+        stream_busy[si] = true;
+        launching += 1;
+        InFlight f;
+        lock.unlock();
+        const bool ok = launch_batch(reqs, si, &f);
+        lock.lock();
+        launching -= 1;
+        if (ok) {
+          f.reqs.swap(reqs);
+          batches += 1;
+          if (f.reqs.size() > max_batch) max_batch = f.reqs.size();
+          inflight.push_back(std::move(f));
+        } else {
+          stream_busy[si] = false;
           error = MEGO_ECUDA;
           for (const Req& q : reqs) {
             mego_completion c{};
             c.id = q.r.id;
             c.status = MEGO_ECUDA;
             c.n = q.r.n;
+            c.B = -1;
             done.push_back(c);
             arena.release(q.off, q.bytes);
           }
@@ -272,7 +300,7 @@ void mego_server::run() {
         }
       }
     }
-    const bool idle = queue.empty() && admitted.empty() && inflight.empty();
+    const bool idle = !busy();
     if (idle) {
       cv.wait_for(lock, std::chrono::milliseconds(1));
     } else {
@@ -320,6 +348,14 @@ mego_status mego_server_create(const mego_server_cfg* cfg, mego_server** out) {
     }
     s->streams.push_back(st);
     s->stream_busy.push_back(false);
+    void* h = nullptr;
+    if (cudaHostAlloc(&h, slice, cudaHostAllocDefault) != cudaSuccess) {
+      for (cudaStream_t t : s->streams) cudaStreamDestroy(t);
+      for (void* p : s->staging) cudaFreeHost(p);
+      delete s;
+      return MEGO_ECUDA;
+    }
+    s->staging.push_back(h);
   }
   s->worker = std::thread([s] { s->run(); });
   *out = s;
@@ -359,7 +395,7 @@ mego_status mego_server_drain(mego_server* s, double timeout_s) {
   std::unique_lock<std::mutex> lock(s->mu);
   const auto deadline = Clock::now() + std::chrono::duration_cast<Clock::duration>(
                                            std::chrono::duration<double>(timeout_s));
-  while (!(s->queue.empty() && s->admitted.empty() && s->inflight.empty())) {
+  while (s->busy()) {
     if (s->cv.wait_until(lock, deadline) == std::cv_status::timeout &&
         Clock::now() >= deadline)
       return MEGO_ETIMEOUT;
@@ -388,6 +424,7 @@ mego_status mego_server_destroy(mego_server* s) {
     cudaEventDestroy(f.done);
   }
   for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
+  for (void* p : s->staging) cudaFreeHost(p);
   delete s;
   return MEGO_OK;
 }

@@ -24,7 +24,7 @@ def _alone(w_h, x_h, rid):
     mego.mego_resample_gather(w, 0, B_dev, SEED, rid & 0xFFFFFFFF, mego.MEGOPOLIS, x_in=x,
                               x_out=x_out, layout=mego.LAYOUT_AOS4, anc=anc)
     torch.cuda.synchronize()
-    return anc.cpu().numpy(), x_out.cpu().numpy()
+    return anc.cpu().numpy(), x_out.cpu().numpy(), int(B_dev.item())
 
 
 def _requests(count, seed, lo=10.0, hi=15.0):
@@ -52,10 +52,12 @@ def test_served_results_equal_alone_under_a_small_budget():
     assert all(c[3] > 0 for c in done)
     assert stats["batches"] > 1 and stats["max_batch"] > 1      # batching happened
     assert stats["peak_arena_bytes"] <= 8 * 40 * biggest + (4 << 20)
+    B_of = {c[0]: c[4] for c in done}
     for rid, w, x, anc, x_out in reqs:
-        a_ref, x_ref = _alone(w.numpy(), x.numpy(), rid)
+        a_ref, x_ref, B_ref = _alone(w.numpy(), x.numpy(), rid)
         assert np.array_equal(anc.numpy(), a_ref), rid
         assert np.array_equal(x_out.numpy(), x_ref), rid
+        assert B_of[rid] == B_ref, rid                # the completion reports the bound's B
 
 
 def test_submit_poll_drain_and_rejections():
@@ -75,5 +77,5 @@ def test_submit_poll_drain_and_rejections():
     assert ei.value.status == mego.MEGO_ENOMEM
     server.close()
     for rid, w, x, anc, x_out in reqs:
-        a_ref, x_ref = _alone(w.numpy(), x.numpy(), rid)
+        a_ref, x_ref, _ = _alone(w.numpy(), x.numpy(), rid)
         assert np.array_equal(anc.numpy(), a_ref) and np.array_equal(x_out.numpy(), x_ref)
