@@ -51,8 +51,13 @@ struct PlanHeader {
   uint32_t count;
   uint32_t total_items;
   uint32_t total_chunks;
-  uint32_t pad[3];
+  uint32_t pad;
+  // The batch's most expensive filter, whose items the queue hands out first
+  // (its chains set the length of the launch): (bits of float((B + 1) x
+  // items) << 32) | ~f, the largest wins (ties: the lowest f); 0 = none.
+  unsigned long long heavy;
 };
+static_assert(sizeof(PlanHeader) == 32, "plan header layout");
 
 struct PlanLayout {
   size_t filters, item_prefix, chunk_prefix, B, status, q, parts, total;
@@ -105,6 +110,32 @@ __device__ __forceinline__ uint32_t find_owner(const uint32_t* prefix, uint32_t 
   return lo;
 }
 
+__host__ __device__ inline unsigned long long heavy_key(float cost, uint32_t f) {
+  uint32_t bits;
+  memcpy(&bits, &cost, sizeof bits);
+  return (static_cast<unsigned long long>(bits) << 32) | static_cast<uint32_t>(~f);
+}
+
+// Queue position -> (filter, item within it): the heavy filter's items come
+// first, then every other filter's in plan order.
+__device__ __forceinline__ uint32_t item_owner(const uint32_t* ip, uint32_t count,
+                                               unsigned long long heavy, uint32_t item,
+                                               uint32_t* local) {
+  if ((heavy >> 32) != 0u) {
+    const uint32_t h = ~static_cast<uint32_t>(heavy);
+    const uint32_t nh = __ldg(ip + h + 1) - __ldg(ip + h);
+    if (item < nh) {
+      *local = item;
+      return h;
+    }
+    item -= nh;
+    if (item >= __ldg(ip + h)) item += nh;
+  }
+  const uint32_t f = find_owner(ip, count, item);
+  *local = item - __ldg(ip + f);
+  return f;
+}
+
 // ---------------------------------------------------------------------------
 // Bound: partial per (filter, chunk), then one warp per filter.
 
@@ -129,6 +160,8 @@ __global__ void __launch_bounds__(kBoundThreads) batch_partials_kernel(const __g
   Partial* parts = reinterpret_cast<Partial*>(a.plan + a.off_parts);
   const uint32_t count = h->count;
   const uint32_t chunk = blockIdx.x;
+  // The finalize that follows picks the heavy filter anew from this bound.
+  if (chunk == 0u && threadIdx.x == 0u) const_cast<PlanHeader*>(h)->heavy = 0ull;
   const uint32_t f = find_owner(cp, count, chunk);
   const uint32_t n = F[f].n;
   const float* w = F[f].w;
@@ -234,6 +267,14 @@ __global__ void __launch_bounds__(256) batch_finalize_kernel(const __grid_consta
   Bout[f] = B;
   Sout[f] = status;
   Qout[f] = q;
+  // Candidate for the heavy filter: cost = (B + 1) x its work items, with the
+  // B the resample will use (a fixed B where the filter has one).
+  const int32_t Beff = F[f].B >= 0 ? F[f].B : B;
+  if (Beff >= 0) {
+    const uint32_t* ip = reinterpret_cast<const uint32_t*>(a.plan + a.off_item_prefix);
+    const float cost = static_cast<float>(Beff + 1) * static_cast<float>(ip[f + 1] - ip[f]);
+    atomicMax(&const_cast<PlanHeader*>(h)->heavy, heavy_key(cost, f));
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -249,13 +290,15 @@ __global__ void __launch_bounds__(256) batch_resample_kernel(const __grid_consta
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t count = h->count;
   const uint32_t total = h->total_items;
+  const unsigned long long heavy = h->heavy;
   int2* win = s_win[threadIdx.x >> 5];
   for (;;) {
     uint32_t item = 0;
     if (lane == 0) item = atomicAdd(&h->next, 1u);
     item = __shfl_sync(0xFFFFFFFFu, item, 0);
     if (item >= total) break;
-    const uint32_t f = find_owner(ip, count, item);
+    uint32_t local = 0;
+    const uint32_t f = item_owner(ip, count, heavy, item, &local);
     const FilterDev d = F[f];
     const int B = d.B >= 0 ? d.B : Bb[f];
     if (B < 0) continue;  // the bound failed for this filter: write nothing
@@ -272,7 +315,7 @@ __global__ void __launch_bounds__(256) batch_resample_kernel(const __grid_consta
     p.nw = 1u;
     p.npart = d.n;
     p.S = stream_key(a.K, d.sid);
-    const uint32_t seg_lo = (item - ip[f]) * kItemSegs;
+    const uint32_t seg_lo = local * kItemSegs;
     const uint32_t seg_hi = min(p.nseg, seg_lo + kItemSegs);
     run_segments<VARIANT, P, false, GATHER>(p, a.K, B, seg_lo, seg_hi, lane, win);
   }
@@ -491,6 +534,16 @@ mego_status batch_plan_staged(const mego_filter* h_filters, int32_t count, int v
   }
   ip[count] = static_cast<uint32_t>(it);
   cp[count] = static_cast<uint32_t>(ch);
+  // Heavy filter among those with a fixed B; a bound recomputes it over all.
+  unsigned long long heavy = 0ull;
+  for (int32_t f = 0; f < count; ++f) {
+    if (h_filters[f].B < 0) continue;
+    const float cost = static_cast<float>(h_filters[f].B + 1) *
+                       static_cast<float>(ip[f + 1] - ip[f]);
+    const unsigned long long k = heavy_key(cost, static_cast<uint32_t>(f));
+    if (k > heavy) heavy = k;
+  }
+  reinterpret_cast<PlanHeader*>(host)->heavy = heavy;
   if (cudaMemcpyAsync(d_plan, host, L.parts, cudaMemcpyHostToDevice,
                       static_cast<cudaStream_t>(stream)) != cudaSuccess)
     return MEGO_ECUDA;
