@@ -407,6 +407,49 @@ def _sweep_leg(args, mego, synthetic, torch, dev):
     return out
 
 
+def _partition_leg(args, mego, synthetic, torch, dev):
+    """The partition-size trade-off (Section 5's C1/C2 comparison): at
+    N = 2^22, y = 4, B from Eq. 3, the resample time (median of event-timed
+    launches, L2 flushed, autotuned shape) and MSE/N over K seeds (offspring
+    counts against N w_i / sum w) of Megopolis, Metropolis and C1/C2 for
+    partition sizes of 128..2048 bytes."""
+    import statistics as stats
+    n, y, K = 1 << 22, 4, args.partition_runs
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    w = torch.from_numpy(synthetic.gaussian_weights(n, y, SEED + 10)).to(dev)
+    B_dev, _, _ = mego.mego_compute_B(w, EPS, stream=stream)
+    B = int(B_dev.item())
+    expected = w.double() * (n / w.double().sum())
+    anc = torch.empty(n, dtype=torch.int32, device=dev)
+    cases = [("megopolis", mego.MEGOPOLIS, 0), ("metropolis", mego.METROPOLIS, 0)]
+    for ps in (128, 256, 512, 1024, 2048):
+        cases += [("c1_ps%d" % ps, mego.METROPOLIS_C1, ps), ("c2_ps%d" % ps, mego.METROPOLIS_C2, ps)]
+    out = {"workload": "N=2^22, y=4, B=%d (Eq. 3, eps=0.01), MSE/N over %d seeds" % (B, K)}
+    for name, variant, ps in cases:
+        cfg, _ = mego.mego_autotune(w, B, variant, psize_bytes=ps, anc=anc, reps=2,
+                                    stream=stream)
+        ts = []
+        for _ in range(args.sweep_reps):
+            flush.zero_()
+            _hold(torch, 1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            mego.mego_resample_gather(w, B, None, SEED, 0, variant, ps, anc=anc, cfg=cfg,
+                                      stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            ts.append(a.elapsed_time(b))
+        se = []
+        for k in range(K):
+            mego.mego_resample_gather(w, B, None, 5000 + k, 0, variant, ps, anc=anc, cfg=cfg,
+                                      stream=stream)
+            o = torch.bincount(anc.long(), minlength=n).double()
+            se.append(float(((o - expected) ** 2).sum()))
+        out[name] = {"ms": stats.median(ts), "mse_per_n": sum(se) / len(se) / n}
+    return out
+
+
 def run_reference(args):
     """The reference arm: the CPU oracle as it stands, timed on the host."""
     world, rank, _ = _dist()
@@ -681,6 +724,8 @@ def run_gpu(args):
     serving = _serving_leg(args, mego, synthetic, torch, dev) if args.serve_requests > 0 else None
     sir = _sir_leg(args, mego, synthetic, torch, dev) if args.sir_trajectories > 0 else None
     sweep = _sweep_leg(args, mego, synthetic, torch, dev) if args.sweep_reps > 0 else None
+    partition = (_partition_leg(args, mego, synthetic, torch, dev)
+                 if args.partition_runs > 0 and args.sweep_reps > 0 else None)
 
     if rank != 0:
         if dist is not None:
@@ -758,6 +803,7 @@ def run_gpu(args):
         "serving": serving,
         "sir_filter": sir,
         "scaling_sweep_resample_ms": sweep,
+        "partition_tradeoff": partition,
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": 4 * N * len(YS),
@@ -857,6 +903,8 @@ def main():
     ap.add_argument("--sir-trajectories", type=int, default=4,
                     help="trajectories in the SIR filter leg (0 skips it)")
     ap.add_argument("--sir-runs", type=int, default=4)
+    ap.add_argument("--partition-runs", type=int, default=16,
+                    help="seeds per variant for the C1/C2 partition trade-off (0: skip)")
     ap.add_argument("--sweep-reps", type=int, default=7,
                     help="timed launches per cell of the N x y sweep (0 skips it)")
     ap.add_argument("--case", choices=sorted(PROFILE_CASES),
