@@ -42,10 +42,27 @@ N = 1 << 20
 YS = (0, 1, 2, 3, 4)
 EPS = 0.01
 SEED = 1
-# Wide multiplies per Megopolis proposal that vary with the iteration: a
-# Philox4x32-10 call has 20, the kernel hoists the 5 that depend only on the
-# particle and the stream, and one call serves five proposals.
+# Work per Megopolis proposal that the method needs, by execution unit (one
+# Philox4x32-10 call serves five proposals; the 5 of its 20 wide multiplies
+# and the 3 of its 20 xors that depend only on the particle and the stream
+# are hoisted):
+#   ALU pipe (16 lanes/cycle per SM sub-partition): the u mask/or, the
+#     compare, the two selects (state weight, accepted column) = 4, plus 17/5
+#     Philox xors and 2/5 byte permutes for the fifth uniform;
+#   FMA-heavy pipe (8 lanes/cycle for a 32x32->64-bit multiply): 15/5;
+#   issue (1 warp instruction/cycle per sub-partition): the above plus the
+#     subtract and multiply of the test and the weight load.
+ALU_OPS_PER_PROPOSAL = 4.0 + 17.0 / 5.0 + 2.0 / 5.0
 MULS_PER_PROPOSAL = 15.0 / 5.0
+INSTR_PER_PROPOSAL = ALU_OPS_PER_PROPOSAL + MULS_PER_PROPOSAL + 2.0 + 1.0
+
+
+def _pipe_peaks(sms, clk_mhz):
+    """Proposals/s each unit allows (x 1e-9: Gproposals/s)."""
+    hz = clk_mhz * 1e6
+    return {"alu_pipe": sms * 64.0 * hz / ALU_OPS_PER_PROPOSAL / 1e9,
+            "fma_heavy_pipe": sms * 32.0 * hz / MULS_PER_PROPOSAL / 1e9,
+            "issue": sms * 128.0 * hz / INSTR_PER_PROPOSAL / 1e9}
 FLUSH_BYTES = 256 << 20
 # Before a run of event-timed launches the stream gets a sleep kernel of this
 # many microseconds, so the host has enqueued the whole run before the GPU
@@ -647,12 +664,10 @@ def run_gpu(args):
     seq_value = N * len(YS) * args.steps / (sum(mego_ms) / 1e3)
     metro_value = N * len(YS) * metro_steps / (sum(metro_ms) / 1e3)
 
-    # Roofline of the dominant kernel: Megopolis at y = 4.  It is bound by
-    # the integer-multiply (FMA-heavy) and ALU pipes that Philox4x32-10 needs,
-    # not by memory: peak proposal rate = SMs x 32 wide 32x32-bit multiplies
-    # per SM-cycle x SM clock / 3 multiplies per proposal (15 of the 20
-    # multiplies of a Philox call vary with the iteration, and one call
-    # serves five proposals).
+    # Roofline of the dominant kernel (the batched Megopolis launch).  It is
+    # bound by arithmetic pipes, not memory (its proposals are served from
+    # L2): the peak is the lowest of the per-unit rates (_pipe_peaks), the
+    # ALU pipe's.
     hbm_peak, peak_src = _peaks()
     k_ms = statistics.mean(bk_ms)
     sumB = float(sum(Bs))
@@ -660,7 +675,8 @@ def run_gpu(args):
     achieved_gbs = alg_bytes / (k_ms / 1e3) / 1e9
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     clk_mhz = clocks.get("sm_max_mhz") or 2070.0
-    peak_gprop = sms * 32.0 * clk_mhz * 1e6 / MULS_PER_PROPOSAL / 1e9
+    pipe_peaks = _pipe_peaks(sms, clk_mhz)
+    peak_gprop = min(pipe_peaks.values())
     achieved_gprop = N * sumB / (k_ms / 1e3) / 1e9
     sink = torch.empty(4096, dtype=torch.float32, device=dev)
     probe_buf = torch.empty(32 << 20, dtype=torch.uint8, device=dev)
@@ -790,9 +806,10 @@ def run_gpu(args):
                      "traffic": _profiled_traffic(),
                      "kernel": "batched Megopolis resample of the five vectors "
                                "(N=2^20 each, B=%s), %.1f us/launch" % (Bs, 1e3 * k_ms),
-                     "peak_derivation": "%d SMs x 32 32x32->64-bit multiplies per SM-cycle "
-                                        "(FMA-heavy pipe) x %.0f MHz / %.1f multiplies per "
-                                        "proposal" % (sms, clk_mhz, MULS_PER_PROPOSAL),
+                     "peak_derivation": "lowest per-unit rate: %d SMs x 64 ALU-pipe lane-ops "
+                                        "per SM-cycle x %.0f MHz / %.1f ALU ops per proposal"
+                                        % (sms, clk_mhz, ALU_OPS_PER_PROPOSAL),
+                     "pipe_peaks_gproposals": pipe_peaks,
                      "memory_view": {"algorithmic_bytes_per_launch": alg_bytes,
                                      "achieved_gbs": achieved_gbs,
                                      "hbm_peak_gbs": hbm_peak, "hbm_peak_source": peak_src,
