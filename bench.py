@@ -711,15 +711,15 @@ def run_gpu(args):
             fused.append(a.elapsed_time(b))
 
     # End to end through the public host-buffer API: every step submits the
-    # five vectors (page-locked host memory) to the serving loop, one stream
-    # per request, which uploads each, runs its bound and resample, copies the
-    # ancestors back; the step ends when all five are on the host.  The client
+    # five vectors (page-locked host memory) to the serving loop, which moves
+    # the weights to the device, runs the bound and the resample and returns
+    # the ancestors; the step ends when all five are on the host.  The client
     # submits longest first by the B each vector had at its previous step (the
-    # completions report it), so the long chain starts first and the short
-    # ones, their copies included, overlap with it.
+    # completions report it): the long chain starts at once on one stream and
+    # the other four follow as one batch on the second, overlapping with it.
     h_w = [torch.from_numpy(synthetic.gaussian_weights(N, y, SEED + y)).pin_memory() for y in YS]
     h_anc = [torch.empty(N, dtype=torch.int32).pin_memory() for _ in YS]
-    server = mego.Server(arena_bytes=512 << 20, seed=SEED, max_batch=1, streams=len(YS),
+    server = mego.Server(arena_bytes=512 << 20, seed=SEED, max_batch=len(YS), streams=2,
                          with_state=False, device=dev)
     e2e_steps = max(3, args.steps // 4)
     last_B = [0] * len(YS)
@@ -826,8 +826,8 @@ def run_gpu(args):
                 "h2d_bytes_per_step": 4 * N * len(YS),
                 "d2h_bytes_per_step": 4 * N * len(YS) + 4 * len(YS),
                 "path": "mego_server_submit x5 (longest first by the previous step's B) + "
-                        "drain per step, one stream per request; host buffers, uploads and "
-                        "downloads (ancestors and B) inside the timed region"},
+                        "drain per step, two streams; page-locked host buffers read and "
+                        "written over the CPU-GPU link inside the timed region"},
         "gpu_launches": launches,
         "cpu_baseline": cpu,
     }

@@ -42,7 +42,7 @@
 extern "C" {
 #endif
 
-#define MEGO_ABI_VERSION 2
+#define MEGO_ABI_VERSION 3
 #define MEGO_N_MAX (1 << 30)
 #define MEGO_B_MAX (1 << 24)
 
@@ -235,6 +235,12 @@ typedef struct mego_filter {
   int32_t B;           /* iterations, or < 0 for the batch bound's value      */
   uint32_t stream_id;  /* random stream of this filter                        */
   int32_t dim;         /* SoA rows to gather; 4 for AoS4                      */
+  const float* w_host; /* optional: the weights in page-locked host memory.
+                          The batched bound then reads them from here (over
+                          the CPU-GPU link, once) and writes the device copy
+                          w that the resample reads, so no separate upload
+                          is needed; mego_batch_bound must then run before
+                          every mego_batch_resample.  NULL: w is read.         */
 } mego_filter;
 
 typedef struct mego_batch {
@@ -318,6 +324,11 @@ typedef struct mego_server_cfg {
   int32_t threads, ppt; /* batch launch shape (0: default)                    */
   int32_t poll_us;      /* worker poll interval while busy (0: 5 us)          */
   int32_t with_state;   /* 1: every request carries AoS4 state; 0: none does  */
+  int32_t host_copies;  /* 0: host buffers that are page-locked are used in
+                           place (weights read by the bound, ancestors and
+                           gathered state written by the resample, over the
+                           CPU-GPU link); others are copied.  1: always copy
+                           through the arena.                                 */
 } mego_server_cfg;
 
 typedef struct mego_server_stats_t {

@@ -61,7 +61,8 @@ class LaunchCfg(ctypes.Structure):
 class Filter(ctypes.Structure):
     _fields_ = [("w", ctypes.c_void_p), ("anc", ctypes.c_void_p), ("x_in", ctypes.c_void_p),
                 ("x_out", ctypes.c_void_p), ("ld", ctypes.c_int64), ("n", ctypes.c_int32),
-                ("B", ctypes.c_int32), ("stream_id", ctypes.c_uint32), ("dim", ctypes.c_int32)]
+                ("B", ctypes.c_int32), ("stream_id", ctypes.c_uint32), ("dim", ctypes.c_int32),
+                ("w_host", ctypes.c_void_p)]
 
 
 class BatchHandle(ctypes.Structure):
@@ -91,7 +92,7 @@ class ServerCfg(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("eps", ctypes.c_double), ("variant", ctypes.c_int32),
                 ("max_batch", ctypes.c_int32), ("streams", ctypes.c_int32),
                 ("threads", ctypes.c_int32), ("ppt", ctypes.c_int32), ("poll_us", ctypes.c_int32),
-                ("with_state", ctypes.c_int32)]
+                ("with_state", ctypes.c_int32), ("host_copies", ctypes.c_int32)]
 
 
 class ServerStats(ctypes.Structure):
@@ -212,6 +213,18 @@ def _dev(t: torch.Tensor, dtype, name: str, numel: Optional[int] = None) -> int:
     if numel is not None and t.numel() < numel:
         raise ValueError("%s has %d elements, needs %d" % (name, t.numel(), numel))
     return t.data_ptr()
+
+
+def _anc_ptr(t: torch.Tensor, numel: int) -> int:
+    """Ancestor output of a batch filter: a CUDA tensor, or a page-locked host
+    tensor that the resample writes directly (over the CPU-GPU link)."""
+    if isinstance(t, torch.Tensor) and not t.is_cuda:
+        if not t.is_pinned() or t.dtype != torch.int32 or not t.is_contiguous() \
+                or t.numel() < numel:
+            raise TypeError("a host anc must be a contiguous page-locked int32 tensor of n "
+                            "elements")
+        return t.data_ptr()
+    return _dev(t, torch.int32, "anc", numel)
 
 
 def _cfg(cfg) -> Optional[LaunchCfg]:
@@ -470,12 +483,18 @@ class Batch:
                 else:
                     dim, ld = 4, 4
             anc = d.get("anc")
+            w_host = d.get("w_host")
+            if w_host is not None and (w_host.is_cuda or not w_host.is_pinned()
+                                       or w_host.dtype != torch.float32
+                                       or not w_host.is_contiguous() or w_host.numel() != n):
+                raise TypeError("w_host must be a contiguous page-locked float32 host tensor "
+                                "of n elements")
             arr[f] = Filter(_dev(w, torch.float32, "w"),
-                            _dev(anc, torch.int32, "anc", n) if anc is not None else None,
+                            _anc_ptr(anc, n) if anc is not None else None,
                             _dev(x_in, torch.float32, "x_in") if x_in is not None else None,
                             _dev(x_out, torch.float32, "x_out") if x_out is not None else None,
                             int(ld), int(n), int(d.get("B", -1)), int(d.get("stream_id", f)),
-                            int(dim))
+                            int(dim), w_host.data_ptr() if w_host is not None else None)
         self._filters = arr
         nbytes = int(lib.mego_batch_plan_bytes(arr, self.count))
         if nbytes == 0:
@@ -569,13 +588,13 @@ class Server:
     def __init__(self, arena_bytes: int, seed: int = 0, eps: float = 0.01,
                  variant: int = MEGOPOLIS, max_batch: int = 256, streams: int = 2,
                  with_state: bool = True, threads: int = 0, ppt: int = 0, poll_us: int = 0,
-                 device=None):
+                 host_copies: bool = False, device=None):
         lib = _load()
         dev = device or torch.device("cuda", torch.cuda.current_device())
         self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device=dev)
         cfg = ServerCfg(self.arena.data_ptr(), int(arena_bytes), int(seed), float(eps),
                         int(variant), int(max_batch), int(streams), int(threads), int(ppt),
-                        int(poll_us), 1 if with_state else 0)
+                        int(poll_us), 1 if with_state else 0, 1 if host_copies else 0)
         self._h = ctypes.c_void_p()
         _check(lib.mego_server_create(ctypes.byref(cfg), ctypes.byref(self._h)),
                "mego_server_create")

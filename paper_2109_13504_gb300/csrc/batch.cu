@@ -43,6 +43,7 @@ struct FilterDev {
   int32_t B;        // >= 0: fixed; < 0: the batch bound's value
   uint32_t sid;
   int32_t dim;
+  const float* w_host;  // non-null: the bound reads here and writes w
 };
 
 struct PlanHeader {
@@ -164,6 +165,7 @@ __global__ void __launch_bounds__(kBoundThreads) batch_partials_kernel(const __g
   if (chunk == 0u && threadIdx.x == 0u) const_cast<PlanHeader*>(h)->heavy = 0ull;
   const uint32_t f = find_owner(cp, count, chunk);
   const uint32_t n = F[f].n;
+  const float* w_host = F[f].w_host;
   const float* w = F[f].w;
   const uint32_t lo = (chunk - cp[f]) * kChunk;
   const uint32_t hi = min(n, lo + kChunk);
@@ -172,10 +174,28 @@ __global__ void __launch_bounds__(kBoundThreads) batch_partials_kernel(const __g
   // index order.
   constexpr int kPer = static_cast<int>(kChunk) / kBoundThreads;
   float v[kPer];
+  if (w_host) {
+    // Page-locked host memory, read once over the CPU-GPU link (plain loads).
 #pragma unroll
-  for (int k = 0; k < kPer; ++k) {
-    const uint32_t i = lo + threadIdx.x + static_cast<uint32_t>(k) * kBoundThreads;
-    v[k] = i < hi ? __ldg(w + i) : 0.0f;
+    for (int k = 0; k < kPer; ++k) {
+      const uint32_t i = lo + threadIdx.x + static_cast<uint32_t>(k) * kBoundThreads;
+      v[k] = i < hi ? w_host[i] : 0.0f;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const uint32_t i = lo + threadIdx.x + static_cast<uint32_t>(k) * kBoundThreads;
+      v[k] = i < hi ? __ldg(w + i) : 0.0f;
+    }
+  }
+  if (w_host) {
+    // Upload: the device copy that the resample reads.
+    float* w_dev = const_cast<float*>(F[f].w);
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const uint32_t i = lo + threadIdx.x + static_cast<uint32_t>(k) * kBoundThreads;
+      if (i < hi) w_dev[i] = v[k];
+    }
   }
   BAcc acc;
 #pragma unroll
@@ -524,7 +544,7 @@ mego_status batch_plan_staged(const mego_filter* h_filters, int32_t count, int v
   for (int32_t f = 0; f < count; ++f) {
     const mego_filter& d = h_filters[f];
     F[f] = FilterDev{d.w, d.anc, d.x_in, d.x_out, d.ld, static_cast<uint32_t>(d.n), d.B,
-                     d.stream_id, d.dim};
+                     d.stream_id, d.dim, d.w_host};
     ip[f] = static_cast<uint32_t>(it);
     cp[f] = static_cast<uint32_t>(ch);
     Bv[f] = d.B;

@@ -114,6 +114,20 @@ size_t slot_bytes(int32_t n) {
   return a(4 * un) + a(4 * un) + a(16 * un) + a(16 * un);
 }
 
+// Device address of page-locked host memory (kernels read and write it over
+// the CPU-GPU link), or null for memory that has to be copied.
+template <typename T>
+T* host_device_ptr(T* p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (at.type != cudaMemoryTypeHost || !at.devicePointer) return nullptr;
+  return static_cast<T*>(at.devicePointer);
+}
+
 }  // namespace
 
 struct mego_server {
@@ -153,6 +167,8 @@ bool mego_server::launch_batch(const std::vector<Req>& reqs, int si, InFlight* f
   cudaStream_t st = streams[si];
   char* base = static_cast<char*>(cfg.d_arena);
   std::vector<mego_filter> filters(reqs.size());
+  std::vector<char> anc_direct(reqs.size(), 0), xo_direct(reqs.size(), 0);
+  const bool direct = cfg.host_copies == 0;
   for (size_t k = 0; k < reqs.size(); ++k) {
     const Req& q = reqs[k];
     const size_t un = static_cast<size_t>(q.r.n);
@@ -162,14 +178,31 @@ bool mego_server::launch_batch(const std::vector<Req>& reqs, int si, InFlight* f
     int32_t* anc = reinterpret_cast<int32_t*>(p + a(4 * un));
     float* xi = reinterpret_cast<float*>(p + 2 * a(4 * un));
     float* xo = reinterpret_cast<float*>(p + 2 * a(4 * un) + a(16 * un));
-    if (cudaMemcpyAsync(w, q.r.h_w, 4 * un, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    // Page-locked host buffers are used in place: the bound reads the
+    // weights (and writes w), the resample writes ancestors and state.  The
+    // state it gathers from is read at random, so it is always uploaded.
+    const float* w_host = direct ? host_device_ptr(q.r.h_w) : nullptr;
+    if (!w_host &&
+        cudaMemcpyAsync(w, q.r.h_w, 4 * un, cudaMemcpyHostToDevice, st) != cudaSuccess)
       return false;
     const bool state = q.r.h_x != nullptr;
     if (state &&
         cudaMemcpyAsync(xi, q.r.h_x, 16 * un, cudaMemcpyHostToDevice, st) != cudaSuccess)
       return false;
+    if (direct) {
+      if (int32_t* h = host_device_ptr(q.r.h_anc)) {
+        anc = h;
+        anc_direct[k] = 1;
+      }
+      if (state) {
+        if (float* h = host_device_ptr(q.r.h_x_out)) {
+          xo = h;
+          xo_direct[k] = 1;
+        }
+      }
+    }
     filters[k] = mego_filter{w, anc, state ? xi : nullptr, state ? xo : nullptr, 4,
-                             q.r.n, -1, static_cast<uint32_t>(q.r.id), state ? 4 : 0};
+                             q.r.n, -1, static_cast<uint32_t>(q.r.id), state ? 4 : 0, w_host};
   }
   // One gather layout per batch: all with state or all without.
   f->plan_bytes = mego_batch_plan_bytes(filters.data(), static_cast<int32_t>(filters.size()));
@@ -186,10 +219,10 @@ bool mego_server::launch_batch(const std::vector<Req>& reqs, int si, InFlight* f
   ok = ok && mego_batch_resample(&f->batch, st) == MEGO_OK;
   for (size_t k = 0; ok && k < reqs.size(); ++k) {
     const Req& q = reqs[k];
-    if (q.r.h_anc)
+    if (q.r.h_anc && !anc_direct[k])
       ok = cudaMemcpyAsync(q.r.h_anc, filters[k].anc, 4 * static_cast<size_t>(q.r.n),
                            cudaMemcpyDeviceToHost, st) == cudaSuccess;
-    if (ok && q.r.h_x_out && filters[k].x_out)
+    if (ok && q.r.h_x_out && filters[k].x_out && !xo_direct[k])
       ok = cudaMemcpyAsync(q.r.h_x_out, filters[k].x_out, 16 * static_cast<size_t>(q.r.n),
                            cudaMemcpyDeviceToHost, st) == cudaSuccess;
   }

@@ -135,3 +135,39 @@ def test_batch_bad_filter_is_isolated():
     assert (filters[2]["anc"].cpu().numpy() == -9).all()
     for f in (0, 1, 3, 4, 5):
         assert st[f] == mego.MEGO_OK and (filters[f]["anc"].cpu().numpy() >= 0).all()
+
+
+def test_host_weights_and_host_ancestors_in_place():
+    """Filters whose weights sit in page-locked host memory (w_host: the bound
+    reads them over the CPU-GPU link and writes the device copy w) and whose
+    ancestors go straight to page-locked host memory give the same B, the
+    same device copy and the same ancestors as the all-device batch."""
+    ws = _make(12, 9, sizes=[1, 33, 4096, 4097, 70000, 1 << 20]) + _make(6, 10)
+    dev_f, host_f = [], []
+    for f, w_h in enumerate(ws):
+        n = w_h.size
+        dev_f.append({"w": torch.from_numpy(w_h).to(DEV),
+                      "anc": torch.empty(n, dtype=torch.int32, device=DEV),
+                      "B": 9 if f == 2 else -1, "stream_id": 40 + f})
+        host_f.append({"w": torch.full((n,), float("nan"), dtype=torch.float32, device=DEV),
+                       "w_host": torch.from_numpy(w_h).pin_memory(),
+                       "anc": torch.full((n,), -5, dtype=torch.int32).pin_memory(),
+                       "B": 9 if f == 2 else -1, "stream_id": 40 + f})
+    ref = mego.Batch(dev_f, seed=SEED)
+    ref.bound(0.01)
+    ref.resample()
+    got = mego.Batch(host_f, seed=SEED)
+    for _ in range(2):                       # the plan replays the same way
+        got.bound(0.01)
+        got.resample()
+        torch.cuda.synchronize()
+        assert np.array_equal(got.B.cpu().numpy(), ref.B.cpu().numpy())
+        for d, h in zip(dev_f, host_f):
+            assert torch.equal(h["w"], d["w"])
+            assert np.array_equal(h["anc"].numpy(), d["anc"].cpu().numpy())
+        for h in host_f:
+            h["anc"].fill_(-5)
+            h["w"].fill_(float("nan"))
+    with pytest.raises(TypeError):           # w_host must be page-locked
+        mego.Batch([{"w": dev_f[0]["w"], "w_host": torch.from_numpy(ws[0]),
+                     "anc": dev_f[0]["anc"]}], seed=SEED)

@@ -79,3 +79,27 @@ def test_submit_poll_drain_and_rejections():
     for rid, w, x, anc, x_out in reqs:
         a_ref, x_ref, _ = _alone(w.numpy(), x.numpy(), rid)
         assert np.array_equal(anc.numpy(), a_ref) and np.array_equal(x_out.numpy(), x_ref)
+
+
+@pytest.mark.parametrize("mode", ["copies", "pageable"])
+def test_copied_buffers_match_direct_ones(mode):
+    """Page-locked buffers are used in place by default; with host_copies the
+    server copies them through the arena, and pageable buffers are always
+    copied.  All three give the same results."""
+    t, reqs = _requests(12, 3, 8.0, 14.0)
+    if mode == "pageable":
+        reqs = [(rid, w.clone(), x.clone(), anc.clone(), x_out.clone())
+                for rid, w, x, anc, x_out in reqs]
+        assert not reqs[0][1].is_pinned()
+    server = mego.Server(arena_bytes=256 << 20, seed=SEED, max_batch=4, streams=2,
+                         host_copies=(mode == "copies"))
+    for r in reqs:
+        server.submit(*r)
+    server.drain(60.0)
+    done = server.poll()
+    server.close()
+    assert len(done) == len(reqs) and all(c[1] == mego.MEGO_OK for c in done)
+    for rid, w, x, anc, x_out in reqs:
+        a_ref, x_ref, _ = _alone(w.numpy(), x.numpy(), rid)
+        assert np.array_equal(anc.numpy(), a_ref), rid
+        assert np.array_equal(x_out.numpy(), x_ref), rid
