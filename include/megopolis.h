@@ -79,9 +79,11 @@ typedef enum mego_path {
 /* Launch shape.  Any field 0 selects the library's choice.  The result
  * never depends on these. */
 typedef struct mego_launch_cfg {
-  int32_t threads;      /* CTA size, a multiple of 32 in [64, 256]         */
-  int32_t ppt;          /* particles per thread, 1, 2, 4 or 8 (each a
-                           32-particle segment of one warp)                  */
+  int32_t threads;      /* CTA size, a multiple of 32 in [64, 256]
+                           ([64, 128] with ppt 6)                            */
+  int32_t ppt;          /* particles per thread, 1, 2, 4, 6 (Megopolis
+                           only) or 8 (each a 32-particle segment of one
+                           warp)                                             */
   int32_t path;         /* mego_path                                         */
   int32_t ctas_per_sm;  /* resident CTAs per SM to aim for                   */
 } mego_launch_cfg;
@@ -267,7 +269,11 @@ mego_status mego_batch_bound(const mego_batch* b, double eps, int32_t b_max,
                              void* stream);
 mego_status mego_batch_resample(const mego_batch* b, void* stream);
 /* Shape of the persistent launch (threads 64..256, particles per thread
- * 1, 2 or 4); the grid is always SMs x resident CTAs. */
+ * 1, 2, 4 or 6 -- 6 for Megopolis only, with threads <= 128); the grid is
+ * always SMs x resident CTAs.  A work item is 6 segments for a Megopolis
+ * batch whose filters of >= 2^17 particles hold most of the work, else 4; it
+ * is fixed in the plan, and the plan's default shape takes one item per warp
+ * batch.  Any shape gives the same results. */
 mego_status mego_batch_set_shape(mego_batch* b, int32_t threads, int32_t ppt);
 /* Time every shape on the batch as planned (outputs are overwritten) and
  * keep the fastest. */

@@ -4,7 +4,8 @@
 // Plan (a caller-provided device buffer, written by mego_batch_plan):
 //   header (queue counters, counts) | filter descriptors | item prefix sums |
 //   chunk prefix sums | per-filter B, status, q | bound partials.
-// Resample work items are (filter, 4 consecutive 32-particle segments);
+// Resample work items are (filter, 6 or 4 consecutive 32-particle segments,
+// chosen per plan);
 // warps of a persistent grid take items from a queue (one atomic per item),
 // so filters of very different cost (size times B) balance themselves.  The
 // last warp to leave resets the queue, so the plan can be launched again.
@@ -29,7 +30,25 @@
 namespace mego {
 namespace {
 
-constexpr uint32_t kItemSegs = 4;        // segments (32 particles each) per work item
+// Segments (32 particles each) per work item, fixed in the plan: one batch
+// of the default particles per thread.  Megopolis takes six chains per thread
+// (items of 6) when filters of at least 2^17 particles hold most of the
+// segments -- long items over long chains, where the extra ILP pays -- and
+// four otherwise (many small filters: shorter items balance better and the
+// per-item start-up is amortised over fewer chains); Metropolis takes 4.
+constexpr uint32_t kItemSegsWide = 6;
+constexpr uint32_t kItemSegs = 4;
+constexpr uint64_t kWideMinSegs = (1u << 17) / 32u;
+uint32_t item_segs_for(int variant, const mego_filter* h, int32_t count) {
+  if (variant != MEGO_MEGOPOLIS) return kItemSegs;
+  uint64_t big = 0, all = 0;
+  for (int32_t f = 0; f < count; ++f) {
+    const uint64_t nseg = (static_cast<uint64_t>(h[f].n) + 31u) / 32u;
+    all += nseg;
+    if (nseg >= kWideMinSegs) big += nseg;
+  }
+  return 2u * big >= all ? kItemSegsWide : kItemSegs;
+}
 constexpr uint32_t kChunk = 4096;        // weights per bound work item
 constexpr int kBoundThreads = 256;       // 16 weights per thread per chunk
 
@@ -52,7 +71,7 @@ struct PlanHeader {
   uint32_t count;
   uint32_t total_items;
   uint32_t total_chunks;
-  uint32_t pad;
+  uint32_t item_segs;    // segments per work item
   // The batch's most expensive filter, whose items the queue hands out first
   // (its chains set the length of the launch): (bits of float((B + 1) x
   // items) << 32) | ~f, the largest wins (ties: the lowest f); 0 = none.
@@ -301,7 +320,7 @@ __global__ void __launch_bounds__(256) batch_finalize_kernel(const __grid_consta
 // Persistent resample over the work queue.
 
 template <int VARIANT, int P, int GATHER>
-__global__ void __launch_bounds__(256) batch_resample_kernel(const __grid_constant__ BatchArgs a) {
+__global__ void __launch_bounds__(max_threads_for(P)) batch_resample_kernel(const __grid_constant__ BatchArgs a) {
   __shared__ int2 s_win[kMaxWarps][32];
   PlanHeader* h = reinterpret_cast<PlanHeader*>(a.plan);
   const FilterDev* F = reinterpret_cast<const FilterDev*>(a.plan + a.off_filters);
@@ -311,6 +330,7 @@ __global__ void __launch_bounds__(256) batch_resample_kernel(const __grid_consta
   const uint32_t count = h->count;
   const uint32_t total = h->total_items;
   const unsigned long long heavy = h->heavy;
+  const uint32_t item_segs = h->item_segs;
   int2* win = s_win[threadIdx.x >> 5];
   for (;;) {
     uint32_t item = 0;
@@ -335,8 +355,8 @@ __global__ void __launch_bounds__(256) batch_resample_kernel(const __grid_consta
     p.nw = 1u;
     p.npart = d.n;
     p.S = stream_key(a.K, d.sid);
-    const uint32_t seg_lo = local * kItemSegs;
-    const uint32_t seg_hi = min(p.nseg, seg_lo + kItemSegs);
+    const uint32_t seg_lo = local * item_segs;
+    const uint32_t seg_hi = min(p.nseg, seg_lo + item_segs);
     run_segments<VARIANT, P, false, GATHER>(p, a.K, B, seg_lo, seg_hi, lane, win);
   }
   // The last warp out resets the queue for the next launch of this plan.
@@ -368,6 +388,9 @@ cudaError_t launch_batch_p(int ppt, int grid, int threads, const BatchArgs& a, c
     case 1: return launch_batch_one<V, 1, G>(grid, threads, a, st);
     case 2: return launch_batch_one<V, 2, G>(grid, threads, a, st);
     case 4: return launch_batch_one<V, 4, G>(grid, threads, a, st);
+    case 6:
+      if constexpr (V == kMegopolis) return launch_batch_one<V, 6, G>(grid, threads, a, st);
+      return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
 }
@@ -378,6 +401,9 @@ const void* batch_ptr_p(int ppt) {
     case 1: return batch_ptr_one<V, 1, G>();
     case 2: return batch_ptr_one<V, 2, G>();
     case 4: return batch_ptr_one<V, 4, G>();
+    case 6:
+      if constexpr (V == kMegopolis) return batch_ptr_one<V, 6, G>();
+      return nullptr;
     default: return nullptr;
   }
 }
@@ -531,7 +557,9 @@ mego_status batch_plan_staged(const mego_filter* h_filters, int32_t count, int v
     host = static_cast<unsigned char*>(staging);
     std::memset(host, 0, L.parts);
   }
+  const uint32_t item_segs = item_segs_for(variant, h_filters, count);
   PlanHeader hdr{};
+  hdr.item_segs = item_segs;
   hdr.count = static_cast<uint32_t>(count);
   hdr.total_items = static_cast<uint32_t>(items);
   hdr.total_chunks = static_cast<uint32_t>(chunks);
@@ -549,9 +577,11 @@ mego_status batch_plan_staged(const mego_filter* h_filters, int32_t count, int v
     cp[f] = static_cast<uint32_t>(ch);
     Bv[f] = d.B;
     const uint64_t nseg = (static_cast<uint64_t>(d.n) + 31u) / 32u;
-    it += (nseg + kItemSegs - 1) / kItemSegs;
+    it += (nseg + item_segs - 1) / item_segs;
     ch += (static_cast<uint64_t>(d.n) + kChunk - 1) / kChunk;
   }
+  reinterpret_cast<PlanHeader*>(host)->total_items = static_cast<uint32_t>(it);
+  items = it;
   ip[count] = static_cast<uint32_t>(it);
   cp[count] = static_cast<uint32_t>(ch);
   // Heavy filter among those with a fixed B; a bound recomputes it over all.
@@ -580,17 +610,17 @@ mego_status batch_plan_staged(const mego_filter* h_filters, int32_t count, int v
   out->d_B = reinterpret_cast<int32_t*>(static_cast<unsigned char*>(d_plan) + L.B);
   out->d_status = reinterpret_cast<int32_t*>(static_cast<unsigned char*>(d_plan) + L.status);
   out->d_q = reinterpret_cast<double*>(static_cast<unsigned char*>(d_plan) + L.q);
-  // Default shape: Megopolis chains are bound by instruction issue, and four
-  // independent chains per thread (one whole work item per warp) hide the
-  // generator's latency better than more resident warps; Metropolis is bound
-  // by scattered loads and takes two.
-  const int ppt = variant == MEGO_MEGOPOLIS ? 4 : 2;
-  out->cfg.threads = 256;
+  // Default shape: Megopolis takes one whole work item per warp (six chains
+  // per thread in 128-thread CTAs, or four in 256-thread CTAs, following the
+  // item size); Metropolis is bound by scattered loads and takes two.
+  const int ppt = variant == MEGO_MEGOPOLIS ? static_cast<int>(item_segs) : 2;
+  const int threads = ppt == 6 ? 128 : 256;
+  out->cfg.threads = threads;
   out->cfg.ppt = ppt;
   out->cfg.path = MEGO_PATH_GLOBAL;
   out->cfg.ctas_per_sm = 0;
   int grid = 0;
-  const mego_status s = shape_for(variant, out->gather, 256, ppt, &grid);
+  const mego_status s = shape_for(variant, out->gather, threads, ppt, &grid);
   if (s != MEGO_OK) return s;
   out->grid = grid;
   return MEGO_OK;
@@ -628,7 +658,8 @@ mego_status mego_batch_resample(const mego_batch* b, void* stream) {
 
 mego_status mego_batch_set_shape(mego_batch* b, int32_t threads, int32_t ppt) {
   using namespace mego;
-  if (!b || threads < 64 || threads > 256 || threads % 32 || (ppt != 1 && ppt != 2 && ppt != 4))
+  if (!b || threads < 64 || threads > (ppt == 6 ? 128 : 256) || threads % 32 ||
+      (ppt != 1 && ppt != 2 && ppt != 4 && ppt != 6))
     return MEGO_EINVAL;
   int grid = 0;
   const mego_status s = shape_for(b->variant, b->gather, threads, ppt, &grid);
@@ -649,7 +680,7 @@ mego_status mego_batch_autotune(mego_batch* b, int32_t reps, float* best_ms, voi
     return MEGO_ECUDA;
   }
   const int threads_c[] = {64, 128, 256};
-  const int ppt_c[] = {1, 2, 4};
+  const int ppt_c[] = {1, 2, 4, 6};
   int best_t = b->cfg.threads, best_p = b->cfg.ppt;
   float best = 1e30f;
   mego_status status = MEGO_OK;

@@ -104,14 +104,21 @@ mego_status choose_shape(int variant, uint32_t n, int gather, const mego_launch_
   DevInfo di;
   if (!dev_info(&di)) return MEGO_ECUDA;
   const uint32_t nseg = (n + 31u) / 32u;
-  int threads = (cfg && cfg->threads) ? cfg->threads : 256;
-  if (threads < 64 || threads > 256 || threads % 32) return MEGO_EINVAL;
   int ppt = (cfg && cfg->ppt) ? cfg->ppt : 0;
   if (ppt == 0) {
+    // Enough segments per SM for several batches per warp: the widest ILP
+    // (Megopolis: six chains per thread in 128-thread CTAs).
     const uint64_t seg_per_sm = nseg / static_cast<uint64_t>(di.sms);
-    ppt = seg_per_sm >= 128 ? 4 : (seg_per_sm >= 32 ? 2 : 1);
+    if (variant == MEGO_MEGOPOLIS && seg_per_sm >= 192)
+      ppt = 6;
+    else
+      ppt = seg_per_sm >= 128 ? 4 : (seg_per_sm >= 32 ? 2 : 1);
   }
-  if (ppt != 1 && ppt != 2 && ppt != 4 && ppt != 8) return MEGO_EINVAL;
+  if (ppt != 1 && ppt != 2 && ppt != 4 && ppt != 6 && ppt != 8) return MEGO_EINVAL;
+  if (ppt == 6 && variant != MEGO_MEGOPOLIS) return MEGO_EINVAL;
+  const int max_threads = ppt == 6 ? 128 : 256;
+  int threads = (cfg && cfg->threads) ? cfg->threads : max_threads;
+  if (threads < 64 || threads > max_threads || threads % 32) return MEGO_EINVAL;
   const size_t w_bytes = (static_cast<size_t>(n) * 4u + 15u) & ~static_cast<size_t>(15u);
   int path = (cfg && cfg->path) ? cfg->path : MEGO_PATH_AUTO;
   if (path == MEGO_PATH_AUTO)
@@ -470,7 +477,7 @@ mego_status mego_autotune(const float* d_w, int32_t n, int32_t B, int variant,
     return MEGO_ECUDA;
   }
   const int threads_c[] = {64, 128, 256};
-  const int ppt_c[] = {1, 2, 4, 8};
+  const int ppt_c[] = {1, 2, 4, 6, 8};
   const int path_c[] = {MEGO_PATH_GLOBAL, MEGO_PATH_SMEM};
   mego_launch_cfg win{0, 0, 0, 0};
   float win_ms = 1e30f;

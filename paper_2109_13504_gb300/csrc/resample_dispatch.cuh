@@ -53,6 +53,9 @@ cudaError_t by_ppt(const LaunchShape& s, const ResampleArgs& a, cudaStream_t st)
     case 1: return launch_one<V, 1, S, G>(s, a, st);
     case 2: return launch_one<V, 2, S, G>(s, a, st);
     case 4: return launch_one<V, 4, S, G>(s, a, st);
+    case 6:
+      if constexpr (V == kMegopolis) return launch_one<V, 6, S, G>(s, a, st);
+      return cudaErrorInvalidValue;
     case 8: return launch_one<V, 8, S, G>(s, a, st);
     default: return cudaErrorInvalidValue;
   }
@@ -64,6 +67,9 @@ const void* ptr_by_ppt(int ppt) {
     case 1: return ptr_one<V, 1, S, G>();
     case 2: return ptr_one<V, 2, S, G>();
     case 4: return ptr_one<V, 4, S, G>();
+    case 6:
+      if constexpr (V == kMegopolis) return ptr_one<V, 6, S, G>();
+      return nullptr;
     case 8: return ptr_one<V, 8, S, G>();
     default: return nullptr;
   }

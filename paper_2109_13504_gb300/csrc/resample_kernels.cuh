@@ -49,6 +49,11 @@ struct ResampleArgs {
 // (wrapped partition base of the warp's first segment, offset o^(b)).
 constexpr int kMaxWarps = 8;
 
+// Largest CTA a kernel with P particles per thread is compiled for.  Six
+// chains per thread (Megopolis) need ~160 registers; a 128-thread bound lets
+// the compiler use them and still fit three CTAs per SM.
+constexpr int max_threads_for(int P) { return P == 6 ? 128 : 256; }
+
 extern __shared__ float4 g_dyn_smem[];
 
 constexpr uint32_t kStageChunk = 32768u;
@@ -422,7 +427,7 @@ __device__ __forceinline__ void run_segments(const Problem& a, const RoundKeys& 
 }
 
 template <int VARIANT, int P, bool SMEM, int GATHER>
-__global__ void __launch_bounds__(256) resample_kernel(const __grid_constant__ ResampleArgs a) {
+__global__ void __launch_bounds__(max_threads_for(P)) resample_kernel(const __grid_constant__ ResampleArgs a) {
   __shared__ int2 s_win[kMaxWarps][32];
   const int B = a.B_dev ? *a.B_dev : a.B;
   if (B < 0) return;  // device-side bound failed: write nothing

@@ -71,13 +71,16 @@ def test_batch_graph_replay_and_shapes_and_autotune():
     batch.resample()
     torch.cuda.synchronize()
     ref = [d["anc"].clone() for d in filters]
-    for threads, ppt in [(64, 1), (128, 2), (256, 4)]:
+    assert batch.shape["ppt"] == 4        # small filters: items of 4, four chains per thread
+    for threads, ppt in [(64, 1), (128, 2), (256, 4), (64, 6), (128, 6)]:
         batch.set_shape(threads, ppt)
         for d in filters:
             d["anc"].fill_(-1)
         batch.resample()
         torch.cuda.synchronize()
         assert all(torch.equal(a, d["anc"]) for a, d in zip(ref, filters))
+    with pytest.raises(mego.MegoError):      # six per thread needs CTAs of <= 128
+        batch.set_shape(256, 6)
     ms = batch.autotune(reps=2)
     assert ms > 0 and batch.shape["threads"] in (64, 128, 256)
     side = torch.cuda.Stream()
@@ -171,3 +174,31 @@ def test_host_weights_and_host_ancestors_in_place():
     with pytest.raises(TypeError):           # w_host must be page-locked
         mego.Batch([{"w": dev_f[0]["w"], "w_host": torch.from_numpy(ws[0]),
                      "anc": dev_f[0]["anc"]}], seed=SEED)
+
+
+def test_large_filters_take_six_chains_per_thread():
+    """A batch dominated by filters of >= 2^17 particles is planned with items
+    of six segments and six chains per thread; every shape (including ones
+    that leave part of an item's batch empty) gives the same ancestors."""
+    ws = _make(3, 12, sizes=[1 << 18, (1 << 17) + 33, 5000])
+    filters = [{"w": torch.from_numpy(w_h).to(DEV),
+                "anc": torch.empty(w_h.size, dtype=torch.int32, device=DEV),
+                "B": -1, "stream_id": 70 + f} for f, w_h in enumerate(ws)]
+    batch = mego.Batch(filters, seed=SEED)
+    assert batch.shape["ppt"] == 6 and batch.shape["threads"] == 128
+    batch.bound(0.01)
+    batch.resample()
+    torch.cuda.synchronize()
+    ref = [d["anc"].clone() for d in filters]
+    Bb = batch.B.cpu().numpy()
+    for f, d in enumerate(filters):
+        alone = mego.mego_resample_gather(d["w"], int(Bb[f]), None, SEED, d["stream_id"],
+                                          mego.MEGOPOLIS, anc=torch.empty_like(d["anc"]))[0]
+        assert torch.equal(alone, ref[f]), f
+    for threads, ppt in [(64, 6), (256, 4), (128, 2), (64, 1)]:
+        batch.set_shape(threads, ppt)
+        for d in filters:
+            d["anc"].fill_(-1)
+        batch.resample()
+        torch.cuda.synchronize()
+        assert all(torch.equal(a, d["anc"]) for a, d in zip(ref, filters)), (threads, ppt)

@@ -58,13 +58,20 @@ def test_small_config_bit_exact(variant):
 
 @pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("path", [mego.PATH_GLOBAL, mego.PATH_SMEM])
-@pytest.mark.parametrize("ppt", [1, 2, 4, 8])
-@pytest.mark.parametrize("threads", [64, 256])
+@pytest.mark.parametrize("ppt", [1, 2, 4, 6, 8])
+@pytest.mark.parametrize("threads", [64, 128, 256])
 def test_launch_shape_invariance(variant, path, ppt, threads):
     n = 4096 + 1000 + 3
     w_h = synthetic.gaussian_weights(n, 3.0, 2)
+    cfg = {"threads": threads, "ppt": ppt, "path": path}
+    if ppt == 6 and (variant != mego.MEGOPOLIS or threads > 128):
+        # six chains per thread: Megopolis only, in CTAs of at most 128 threads
+        with pytest.raises(mego.MegoError) as ei:
+            _anc(w_h, 45, 9, variant, cfg=cfg)
+        assert ei.value.status == mego.MEGO_EINVAL
+        return
     ref = oracle.resample(w_h, 45, 9, variant)
-    got = _anc(w_h, 45, 9, variant, cfg={"threads": threads, "ppt": ppt, "path": path})
+    got = _anc(w_h, 45, 9, variant, cfg=cfg)
     assert np.array_equal(got, ref)
 
 
@@ -328,11 +335,11 @@ def test_autotune_picks_a_shape_and_keeps_results_exact():
     w_h = synthetic.gaussian_weights(n, 3.0, 13)
     w = _gpu(w_h)
     cfg, ms = mego.mego_autotune(w, 60, mego.MEGOPOLIS)
-    assert cfg["threads"] in (64, 128, 256) and cfg["ppt"] in (1, 2, 4, 8)
+    assert cfg["threads"] in (64, 128, 256) and cfg["ppt"] in (1, 2, 4, 6, 8)
     assert cfg["path"] in (mego.PATH_GLOBAL, mego.PATH_SMEM) and ms > 0
     got = _anc(w_h, 60, 5, mego.MEGOPOLIS)            # no cfg: the tuned shape
     assert np.array_equal(got, oracle.resample(w_h, 60, 5, mego.MEGOPOLIS))
-    for ppt in (1, 2, 4, 8):
+    for ppt in (1, 2, 4, 6, 8):
         got = _anc(w_h, 60, 5, mego.MEGOPOLIS, cfg={"ppt": ppt, "threads": 128})
         assert np.array_equal(got, oracle.resample(w_h, 60, 5, mego.MEGOPOLIS))
 
