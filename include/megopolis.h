@@ -330,11 +330,12 @@ typedef struct mego_server_cfg {
   int32_t threads, ppt; /* batch launch shape (0: default)                    */
   int32_t poll_us;      /* worker poll interval while busy (0: 5 us)          */
   int32_t with_state;   /* 1: every request carries AoS4 state; 0: none does  */
-  int32_t host_copies;  /* 0: host buffers that are page-locked are used in
-                           place (weights read by the bound, ancestors and
-                           gathered state written by the resample, over the
-                           CPU-GPU link); others are copied.  1: always copy
-                           through the arena.                                 */
+  int32_t host_copies;  /* 0: inputs are uploaded by the copy engine;
+                           results go straight into page-locked host buffers
+                           (the resample writes ancestors and gathered state
+                           over the CPU-GPU link), others are copied back.
+                           1: copies both ways.  2: as 0, and the bound also
+                           reads page-locked weights in place.               */
 } mego_server_cfg;
 
 typedef struct mego_server_stats_t {

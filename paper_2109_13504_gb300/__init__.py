@@ -588,13 +588,13 @@ class Server:
     def __init__(self, arena_bytes: int, seed: int = 0, eps: float = 0.01,
                  variant: int = MEGOPOLIS, max_batch: int = 256, streams: int = 2,
                  with_state: bool = True, threads: int = 0, ppt: int = 0, poll_us: int = 0,
-                 host_copies: bool = False, device=None):
+                 host_copies: int = 0, device=None):
         lib = _load()
         dev = device or torch.device("cuda", torch.cuda.current_device())
         self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device=dev)
         cfg = ServerCfg(self.arena.data_ptr(), int(arena_bytes), int(seed), float(eps),
                         int(variant), int(max_batch), int(streams), int(threads), int(ppt),
-                        int(poll_us), 1 if with_state else 0, 1 if host_copies else 0)
+                        int(poll_us), 1 if with_state else 0, int(host_copies))
         self._h = ctypes.c_void_p()
         _check(lib.mego_server_create(ctypes.byref(cfg), ctypes.byref(self._h)),
                "mego_server_create")

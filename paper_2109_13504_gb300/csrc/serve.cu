@@ -168,7 +168,7 @@ bool mego_server::launch_batch(const std::vector<Req>& reqs, int si, InFlight* f
   char* base = static_cast<char*>(cfg.d_arena);
   std::vector<mego_filter> filters(reqs.size());
   std::vector<char> anc_direct(reqs.size(), 0), xo_direct(reqs.size(), 0);
-  const bool direct = cfg.host_copies == 0;
+  const bool direct = cfg.host_copies != 1;
   for (size_t k = 0; k < reqs.size(); ++k) {
     const Req& q = reqs[k];
     const size_t un = static_cast<size_t>(q.r.n);
@@ -178,10 +178,12 @@ bool mego_server::launch_batch(const std::vector<Req>& reqs, int si, InFlight* f
     int32_t* anc = reinterpret_cast<int32_t*>(p + a(4 * un));
     float* xi = reinterpret_cast<float*>(p + 2 * a(4 * un));
     float* xo = reinterpret_cast<float*>(p + 2 * a(4 * un) + a(16 * un));
-    // Page-locked host buffers are used in place: the bound reads the
-    // weights (and writes w), the resample writes ancestors and state.  The
-    // state it gathers from is read at random, so it is always uploaded.
-    const float* w_host = direct ? host_device_ptr(q.r.h_w) : nullptr;
+    // Results go straight into page-locked host buffers (the resample writes
+    // ancestors and state).  Inputs are uploaded by the copy engine, which
+    // runs while other batches hold every SM; with host_copies = 2 the bound
+    // reads page-locked weights itself (and writes w).  The state the
+    // resample gathers from is read at random, so it is always uploaded.
+    const float* w_host = cfg.host_copies == 2 ? host_device_ptr(q.r.h_w) : nullptr;
     if (!w_host &&
         cudaMemcpyAsync(w, q.r.h_w, 4 * un, cudaMemcpyHostToDevice, st) != cudaSuccess)
       return false;

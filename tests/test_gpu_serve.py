@@ -81,18 +81,19 @@ def test_submit_poll_drain_and_rejections():
         assert np.array_equal(anc.numpy(), a_ref) and np.array_equal(x_out.numpy(), x_ref)
 
 
-@pytest.mark.parametrize("mode", ["copies", "pageable"])
+@pytest.mark.parametrize("mode", ["copies", "weights_in_place", "pageable"])
 def test_copied_buffers_match_direct_ones(mode):
-    """Page-locked buffers are used in place by default; with host_copies the
-    server copies them through the arena, and pageable buffers are always
-    copied.  All three give the same results."""
+    """By default inputs are uploaded and results written in place into
+    page-locked buffers; host_copies = 1 copies both ways, 2 also reads the
+    weights in place; pageable buffers are always copied.  All give the same
+    results."""
     t, reqs = _requests(12, 3, 8.0, 14.0)
     if mode == "pageable":
         reqs = [(rid, w.clone(), x.clone(), anc.clone(), x_out.clone())
                 for rid, w, x, anc, x_out in reqs]
         assert not reqs[0][1].is_pinned()
     server = mego.Server(arena_bytes=256 << 20, seed=SEED, max_batch=4, streams=2,
-                         host_copies=(mode == "copies"))
+                         host_copies={"copies": 1, "weights_in_place": 2}.get(mode, 0))
     for r in reqs:
         server.submit(*r)
     server.drain(60.0)
