@@ -18,6 +18,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <utility>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -136,6 +137,24 @@ __host__ __device__ inline unsigned long long heavy_key(float cost, uint32_t f) 
   return (static_cast<unsigned long long>(bits) << 32) | static_cast<uint32_t>(~f);
 }
 
+// Launch with programmatic stream serialization: the kernel may be scheduled
+// while its predecessor drains and waits for it in grid_dependency_wait().
+template <typename... Params, typename... Args>
+cudaError_t launch_after(void (*kernel)(Params...), int grid, int threads, cudaStream_t st,
+                         Args&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(static_cast<unsigned>(grid));
+  cfg.blockDim = dim3(static_cast<unsigned>(threads));
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // Queue position -> (filter, item within it): the heavy filter's items come
 // first, then every other filter's in plan order.
 __device__ __forceinline__ uint32_t item_owner(const uint32_t* ip, uint32_t count,
@@ -180,6 +199,7 @@ __global__ void __launch_bounds__(kBoundThreads) batch_partials_kernel(const __g
   Partial* parts = reinterpret_cast<Partial*>(a.plan + a.off_parts);
   const uint32_t count = h->count;
   const uint32_t chunk = blockIdx.x;
+  grid_launch_dependents();  // the finalize may be scheduled now; it waits for us
   // The finalize that follows picks the heavy filter anew from this bound.
   if (chunk == 0u && threadIdx.x == 0u) const_cast<PlanHeader*>(h)->heavy = 0ull;
   const uint32_t f = find_owner(cp, count, chunk);
@@ -264,6 +284,8 @@ __global__ void __launch_bounds__(256) batch_finalize_kernel(const __grid_consta
   double* Qout = reinterpret_cast<double*>(a.plan + a.off_q);
   const uint32_t f = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const uint32_t lane = threadIdx.x & 31u;
+  grid_launch_dependents();  // the resample may be scheduled now; it waits for us
+  grid_dependency_wait();    // the partials are complete and visible
   if (f >= h->count) return;
   double sum = 0.0;
   float mx = 0.0f;
@@ -327,6 +349,7 @@ __global__ void __launch_bounds__(max_threads_for(P)) batch_resample_kernel(cons
   const uint32_t* ip = reinterpret_cast<const uint32_t*>(a.plan + a.off_item_prefix);
   const int32_t* Bb = reinterpret_cast<const int32_t*>(a.plan + a.off_B);
   const uint32_t lane = threadIdx.x & 31u;
+  grid_dependency_wait();  // the bound's B and heavy filter are complete and visible
   const uint32_t count = h->count;
   const uint32_t total = h->total_items;
   const unsigned long long heavy = h->heavy;
@@ -373,8 +396,7 @@ __global__ void __launch_bounds__(max_threads_for(P)) batch_resample_kernel(cons
 
 template <int V, int P, int G>
 cudaError_t launch_batch_one(int grid, int threads, const BatchArgs& a, cudaStream_t st) {
-  batch_resample_kernel<V, P, G><<<grid, threads, 0, st>>>(a);
-  return cudaGetLastError();
+  return launch_after(batch_resample_kernel<V, P, G>, grid, threads, st, a);
 }
 
 template <int V, int P, int G>
@@ -639,8 +661,9 @@ mego_status mego_batch_bound(const mego_batch* b, double eps, int32_t b_max, voi
   batch_partials_kernel<<<static_cast<unsigned>(b->total_chunks), kBoundThreads, 0, st>>>(a);
   if (cudaGetLastError() != cudaSuccess) return MEGO_ECUDA;
   const unsigned fgrid = static_cast<unsigned>((b->count + 7) / 8);
-  batch_finalize_kernel<<<fgrid, 256, 0, st>>>(a, std::log(eps), b_max);
-  if (cudaGetLastError() != cudaSuccess) return MEGO_ECUDA;
+  if (launch_after(batch_finalize_kernel, static_cast<int>(fgrid), 256, st, a, std::log(eps),
+                   b_max) != cudaSuccess)
+    return MEGO_ECUDA;
   count_launches(2);
   return MEGO_OK;
 }

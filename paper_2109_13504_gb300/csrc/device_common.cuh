@@ -157,6 +157,21 @@ __device__ __forceinline__ uint32_t mego_word(const uint4& x, int q) {
 }
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch.  A kernel launched with the programmatic
+// stream serialization attribute may be scheduled while its predecessor on
+// the stream is still running; grid_dependency_wait() returns once the
+// predecessor has completed and its writes are visible (immediately when
+// there is no such predecessor), so everything that reads the predecessor's
+// results comes after it.  grid_launch_dependents() lets the next such kernel
+// be scheduled before this one finishes.
+__device__ __forceinline__ void grid_dependency_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void grid_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
 // Bulk async copy global -> shared with mbarrier completion (sm_90+ PTX).
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
