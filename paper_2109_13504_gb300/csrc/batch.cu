@@ -137,24 +137,6 @@ __host__ __device__ inline unsigned long long heavy_key(float cost, uint32_t f) 
   return (static_cast<unsigned long long>(bits) << 32) | static_cast<uint32_t>(~f);
 }
 
-// Launch with programmatic stream serialization: the kernel may be scheduled
-// while its predecessor drains and waits for it in grid_dependency_wait().
-template <typename... Params, typename... Args>
-cudaError_t launch_after(void (*kernel)(Params...), int grid, int threads, cudaStream_t st,
-                         Args&&... args) {
-  cudaLaunchConfig_t cfg{};
-  cfg.gridDim = dim3(static_cast<unsigned>(grid));
-  cfg.blockDim = dim3(static_cast<unsigned>(threads));
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
-}
-
 // Queue position -> (filter, item within it): the heavy filter's items come
 // first, then every other filter's in plan order.
 __device__ __forceinline__ uint32_t item_owner(const uint32_t* ip, uint32_t count,
@@ -396,7 +378,7 @@ __global__ void __launch_bounds__(max_threads_for(P)) batch_resample_kernel(cons
 
 template <int V, int P, int G>
 cudaError_t launch_batch_one(int grid, int threads, const BatchArgs& a, cudaStream_t st) {
-  return launch_after(batch_resample_kernel<V, P, G>, grid, threads, st, a);
+  return launch_after(batch_resample_kernel<V, P, G>, dim3(grid), dim3(threads), 0, st, a);
 }
 
 template <int V, int P, int G>
@@ -661,7 +643,7 @@ mego_status mego_batch_bound(const mego_batch* b, double eps, int32_t b_max, voi
   batch_partials_kernel<<<static_cast<unsigned>(b->total_chunks), kBoundThreads, 0, st>>>(a);
   if (cudaGetLastError() != cudaSuccess) return MEGO_ECUDA;
   const unsigned fgrid = static_cast<unsigned>((b->count + 7) / 8);
-  if (launch_after(batch_finalize_kernel, static_cast<int>(fgrid), 256, st, a, std::log(eps),
+  if (launch_after(batch_finalize_kernel, dim3(fgrid), dim3(256), 0, st, a, std::log(eps),
                    b_max) != cudaSuccess)
     return MEGO_ECUDA;
   count_launches(2);

@@ -97,6 +97,7 @@ template <bool LIKELIHOOD>
 __global__ void __launch_bounds__(kReduceThreads)
 partials_kernel(const float* __restrict__ src, uint32_t n, float y,
                 float* __restrict__ w_out, Partial* __restrict__ parts) {
+  grid_launch_dependents();  // the finalize may be scheduled now; it waits for us
   ThreadAcc a;
   const uint32_t stride = gridDim.x * blockDim.x;
   const uint32_t t0 = blockIdx.x * blockDim.x + threadIdx.x;
@@ -153,6 +154,8 @@ finalize_kernel(const Partial* __restrict__ parts, int nparts, uint32_t n, doubl
   // One warp: each lane folds its strided partials in index order, then a
   // fixed shuffle tree combines the lanes.
   // Loads go out eight at a time, ahead of the (order-dependent) merges.
+  grid_launch_dependents();  // a resample launched after us may be scheduled
+  grid_dependency_wait();    // the partials are complete and visible
   Acc a{0.0f, 0, 0.0};
   for (int t0 = threadIdx.x; t0 < nparts; t0 += 8 * 32) {
     Partial p[8];
@@ -231,9 +234,9 @@ cudaError_t launch_partials(const float* src, uint32_t n, bool likelihood, float
 cudaError_t launch_finalize(const Partial* parts, int nparts, uint32_t n, double eps,
                             int32_t b_max, int32_t* d_B, int32_t* d_status, double* d_q,
                             cudaStream_t st) {
-  finalize_kernel<<<1, 32, 0, st>>>(parts, nparts, n, std::log(eps), b_max, d_B, d_status,
-                                    d_q);
-  return cudaGetLastError();
+  return launch_after(finalize_kernel, dim3(1), dim3(32), 0, st,
+                      static_cast<const Partial*>(parts), nparts, n, std::log(eps), b_max, d_B,
+                      d_status, d_q);
 }
 
 cudaError_t launch_probe_read(const void* buf, size_t bytes, int reps, float* sink,

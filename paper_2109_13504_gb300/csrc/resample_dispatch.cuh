@@ -38,8 +38,8 @@ cudaError_t launch_one(const LaunchShape& s, const ResampleArgs& a, cudaStream_t
     const cudaError_t e = enable_large_smem(reinterpret_cast<const void*>(k));
     if (e != cudaSuccess) return e;
   }
-  k<<<s.grid, s.threads, s.smem_bytes, st>>>(a);
-  return cudaGetLastError();
+  return launch_after(k, dim3(static_cast<unsigned>(s.grid)), dim3(static_cast<unsigned>(s.threads)),
+                      s.smem_bytes, st, a);
 }
 
 template <int V, int P, bool S, int G>

@@ -429,6 +429,7 @@ __device__ __forceinline__ void run_segments(const Problem& a, const RoundKeys& 
 template <int VARIANT, int P, bool SMEM, int GATHER>
 __global__ void __launch_bounds__(max_threads_for(P)) resample_kernel(const __grid_constant__ ResampleArgs a) {
   __shared__ int2 s_win[kMaxWarps][32];
+  grid_dependency_wait();  // inputs (weights, a device-side B) written by the predecessor
   const int B = a.B_dev ? *a.B_dev : a.B;
   if (B < 0) return;  // device-side bound failed: write nothing
   if constexpr (SMEM) {
