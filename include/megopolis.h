@@ -52,8 +52,10 @@ typedef enum mego_status {
   MEGO_ENOMEM = 2,    /* caller workspace too small                       */
   MEGO_ECUDA = 3,     /* a CUDA runtime call failed                       */
   MEGO_ETIMEOUT = 4,  /* mego_sync_status: deadline passed                */
-  MEGO_EWEIGHTS = 5   /* device: NaN/Inf/negative or all-zero weights, or
-                         B above the cap                                  */
+  MEGO_EWEIGHTS = 5   /* device: NaN/Inf/negative or all-zero weights,
+                         weights so large that a partial sum leaves the
+                         float range (about 1e32 and above), or B above
+                         the cap                                          */
 } mego_status;
 
 typedef enum mego_variant {
@@ -134,11 +136,14 @@ mego_status mego_resample_gather(const float* d_w, int32_t n, int32_t B,
 /* ----------------------------------------------------------------------
  * Iteration bound, Eq. 3 (Section 3) and Proposition 1 (Eq. 4):
  *   B = ceil(log(eps) / log(1 - E(w)/max(w)))
- * with E(w) the sample mean (summed in double, fixed order) and max(w) the
- * sample maximum.  eps in (0, 1].  E(w) = max(w) or eps = 1 gives B = 0.
+ * with E(w) the sample mean (compensated float-float sums inside each CTA,
+ * double across CTAs, in a fixed order) and max(w) the sample maximum.
+ * eps in (0, 1].  E(w) = max(w) or eps = 1 gives B = 0.
  *   d_B       [1] int32 output: B, or -1 on a device-side error.
  *   d_status  [1] int32 output: MEGO_OK, or MEGO_EWEIGHTS when a weight is
- *             NaN, infinite or negative, all weights are 0, or B > b_max.
+ *             NaN, infinite or negative, all weights are 0, a CTA's partial
+ *             sum leaves the float range (weights of about 1e32 or more), or
+ *             B > b_max.
  *   d_q       [1] double output, the value before the ceiling; may be NULL.
  *   b_max     cap on B, 0 < b_max <= MEGO_B_MAX.
  *   d_ws      caller workspace of at least mego_workspace_bytes(n) bytes,

@@ -222,17 +222,22 @@ __global__ void __launch_bounds__(kBoundThreads) batch_partials_kernel(const __g
 #pragma unroll
   for (int k = 0; k < kPer; ++k)
     if (lo + threadIdx.x + static_cast<uint32_t>(k) * kBoundThreads < hi) acc.add(v[k]);
-  // Fixed-order tree: warp shuffles, then warp 0 over the warp results.
-  double sum = static_cast<double>(acc.s) + static_cast<double>(acc.c);
+  // Fixed-order tree in float-float (no FP64 work per thread: this part's
+  // FP64 pipe is narrow): warp shuffles, then thread 0 over the warp results;
+  // the chunk's partial is converted to double once.
+  FloatFloat sum = ff_from_pair(acc.s, acc.c);
   float mx = acc.mx;
   int bad = acc.bad;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
-    sum += __shfl_down_sync(0xFFFFFFFFu, sum, off);
+    FloatFloat o;
+    o.hi = __shfl_down_sync(0xFFFFFFFFu, sum.hi, off);
+    o.lo = __shfl_down_sync(0xFFFFFFFFu, sum.lo, off);
+    sum = ff_add(sum, o);
     mx = fmaxf(mx, __shfl_down_sync(0xFFFFFFFFu, mx, off));
     bad |= __shfl_down_sync(0xFFFFFFFFu, bad, off);
   }
-  __shared__ double s_sum[kBoundThreads / 32];
+  __shared__ FloatFloat s_sum[kBoundThreads / 32];
   __shared__ float s_mx[kBoundThreads / 32];
   __shared__ int s_bad[kBoundThreads / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -243,15 +248,15 @@ __global__ void __launch_bounds__(kBoundThreads) batch_partials_kernel(const __g
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t = 0.0;
+    FloatFloat t{0.0f, 0.0f};
     float m = 0.0f;
     int b = 0;
     for (int k = 0; k < kBoundThreads / 32; ++k) {
-      t += s_sum[k];
+      t = ff_add(t, s_sum[k]);
       m = fmaxf(m, s_mx[k]);
       b |= s_bad[k];
     }
-    parts[chunk] = Partial{m, b, t};
+    parts[chunk] = Partial{m, b, ff_to_double(t)};
   }
 }
 
@@ -297,7 +302,7 @@ __global__ void __launch_bounds__(256) batch_finalize_kernel(const __grid_consta
   if (lane != 0) return;
   int32_t B = -1, status = kStatusWeights;
   double q = __longlong_as_double(0x7FF8000000000000LL);
-  if (!bad && mx > 0.0f) {
+  if (!bad && mx > 0.0f && isfinite(sum)) {  // an overflowed chunk sum cannot give B
     const double r = sum / (static_cast<double>(F[f].n) * static_cast<double>(mx));
     q = (r >= 1.0) ? 0.0 : log_eps / log1p(-r);
     double c = ceil(q);

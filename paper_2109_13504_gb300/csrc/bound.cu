@@ -1,9 +1,10 @@
 // bound.cu -- weight reduction and the iteration bound (Eq. 3), optionally
 // fused with the likelihood weight (Eq. 12), plus a read-bandwidth probe.
 //
-// Deterministic: a fixed grid writes one partial (max, double sum, bad flag)
-// per CTA; a single CTA then folds the partials in index order.  The result
-// depends only on n and the weight bits.
+// Deterministic: a fixed grid writes one partial (max, sum, bad flag) per CTA
+// (float-float inside the CTA, stored as a double); a single warp then folds
+// the partials in a fixed order.  The result depends only on n and the
+// weight bits.
 #include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -18,13 +19,14 @@ namespace {
 struct Acc {
   float mx;
   int bad;
-  double sum;
+  FloatFloat sum;
 };
 
 // Per-thread accumulator: max, validity and a compensated (Neumaier) float
-// sum s + c, converted to double once per thread.  FP64 operations are slow
-// on this part, so none are used per element.  The compensated sum of a
-// thread's few thousand weights is exact to about 2 ulp of float squared.
+// sum s + c.  No FP64 operation is used per element or in the tree (FP64 is
+// slow on this part): threads combine float-float values and each CTA
+// converts its partial to double once.  The compensated sum of a thread's
+// weights is exact to about 2 ulp of float squared.
 struct ThreadAcc {
   float mx = 0.0f;
   int bad = 0;
@@ -38,42 +40,37 @@ struct ThreadAcc {
                                             : __fadd_rn(__fsub_rn(v, t), s));
     s = t;
   }
-  __device__ __forceinline__ Acc to_acc() const {
-    return Acc{mx, bad, static_cast<double>(s) + static_cast<double>(c)};
-  }
+  __device__ __forceinline__ Acc to_acc() const { return Acc{mx, bad, ff_from_pair(s, c)}; }
 };
 
 __device__ __forceinline__ void acc_merge(Acc& a, const Acc& b) {
   a.bad |= b.bad;
   a.mx = fmaxf(a.mx, b.mx);
-  a.sum += b.sum;
+  a.sum = ff_add(a.sum, b.sum);
+}
+
+__device__ __forceinline__ Acc acc_shfl_down(const Acc& a, int off) {
+  Acc o;
+  o.mx = __shfl_down_sync(0xFFFFFFFFu, a.mx, off);
+  o.bad = __shfl_down_sync(0xFFFFFFFFu, a.bad, off);
+  o.sum.hi = __shfl_down_sync(0xFFFFFFFFu, a.sum.hi, off);
+  o.sum.lo = __shfl_down_sync(0xFFFFFFFFu, a.sum.lo, off);
+  return o;
 }
 
 // Warp then CTA reduction in a fixed tree order; result valid in thread 0.
 __device__ __forceinline__ Acc block_reduce(Acc a) {
   __shared__ Acc s[32];
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    Acc o;
-    o.mx = __shfl_down_sync(0xFFFFFFFFu, a.mx, off);
-    o.bad = __shfl_down_sync(0xFFFFFFFFu, a.bad, off);
-    o.sum = __shfl_down_sync(0xFFFFFFFFu, a.sum, off);
-    acc_merge(a, o);
-  }
+  for (int off = 16; off > 0; off >>= 1) acc_merge(a, acc_shfl_down(a, off));
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0) s[warp] = a;
   __syncthreads();
   if (warp == 0) {
     const int nw = blockDim.x >> 5;
-    a = lane < nw ? s[lane] : Acc{0.0f, 0, 0.0};
+    a = lane < nw ? s[lane] : Acc{0.0f, 0, FloatFloat{0.0f, 0.0f}};
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      Acc o;
-      o.mx = __shfl_down_sync(0xFFFFFFFFu, a.mx, off);
-      o.bad = __shfl_down_sync(0xFFFFFFFFu, a.bad, off);
-      o.sum = __shfl_down_sync(0xFFFFFFFFu, a.sum, off);
-      acc_merge(a, o);
-    }
+    for (int off = 16; off > 0; off >>= 1) acc_merge(a, acc_shfl_down(a, off));
   }
   return a;
 }
@@ -144,7 +141,7 @@ partials_kernel(const float* __restrict__ src, uint32_t n, float y,
     a.add(v);
   }
   const Acc r = block_reduce(a.to_acc());
-  if (threadIdx.x == 0) parts[blockIdx.x] = Partial{r.mx, r.bad, r.sum};
+  if (threadIdx.x == 0) parts[blockIdx.x] = Partial{r.mx, r.bad, ff_to_double(r.sum)};
 }
 
 __global__ void __launch_bounds__(32)
@@ -156,30 +153,39 @@ finalize_kernel(const Partial* __restrict__ parts, int nparts, uint32_t n, doubl
   // Loads go out eight at a time, ahead of the (order-dependent) merges.
   grid_launch_dependents();  // a resample launched after us may be scheduled
   grid_dependency_wait();    // the partials are complete and visible
-  Acc a{0.0f, 0, 0.0};
+  // The partials are few: the fold stays in double.
+  float mx = 0.0f;
+  int bad = 0;
+  double sum = 0.0;
   for (int t0 = threadIdx.x; t0 < nparts; t0 += 8 * 32) {
     Partial p[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k)
       if (t0 + 32 * k < nparts) p[k] = parts[t0 + 32 * k];
 #pragma unroll
-    for (int k = 0; k < 8; ++k)
-      if (t0 + 32 * k < nparts) acc_merge(a, Acc{p[k].mx, p[k].bad, p[k].sum});
+    for (int k = 0; k < 8; ++k) {
+      if (t0 + 32 * k < nparts) {
+        mx = fmaxf(mx, p[k].mx);
+        bad |= p[k].bad;
+        sum += p[k].sum;
+      }
+    }
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
-    Acc o;
-    o.mx = __shfl_down_sync(0xFFFFFFFFu, a.mx, off);
-    o.bad = __shfl_down_sync(0xFFFFFFFFu, a.bad, off);
-    o.sum = __shfl_down_sync(0xFFFFFFFFu, a.sum, off);
-    acc_merge(a, o);
+    mx = fmaxf(mx, __shfl_down_sync(0xFFFFFFFFu, mx, off));
+    bad |= __shfl_down_sync(0xFFFFFFFFu, bad, off);
+    sum += __shfl_down_sync(0xFFFFFFFFu, sum, off);
   }
+  const Acc a{mx, bad, FloatFloat{0.0f, 0.0f}};
   if (threadIdx.x != 0) return;
   int32_t B = -1, status = kStatusWeights;
   double q = __longlong_as_double(0x7FF8000000000000LL);  // NaN
-  if (!a.bad && a.mx > 0.0f) {
+  // A sum that overflowed binary32 inside a chunk (finite weights of order
+  // FLT_MAX / 4096 or more) cannot give B: reported like invalid weights.
+  if (!a.bad && a.mx > 0.0f && isfinite(sum)) {
     // r = E(w) / max(w) with one division; log(eps) comes from the host.
-    const double r = a.sum / (static_cast<double>(n) * static_cast<double>(a.mx));
+    const double r = sum / (static_cast<double>(n) * static_cast<double>(a.mx));
     q = (r >= 1.0) ? 0.0 : log_eps / log1p(-r);
     double c = ceil(q);
     if (c < 0.0) c = 0.0;

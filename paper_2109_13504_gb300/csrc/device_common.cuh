@@ -159,6 +159,35 @@ __device__ __forceinline__ uint32_t mego_word(const uint4& x, int q) {
 }
 
 // ---------------------------------------------------------------------------
+// Float-float sums: hi + lo with |lo| <= ulp(hi) / 2, about 48 significant bits
+// from binary32 arithmetic alone (this part's FP64 pipe is narrow, its FP32
+// pipes are not).  ff_add is Dekker's addition: Knuth's TwoSum of the high
+// parts, the low parts and the rounding error added, then Fast2Sum to
+// renormalise.  The bound adds only non-negative values, so no cancellation
+// degrades it.
+struct FloatFloat {
+  float hi, lo;
+};
+
+// From a compensated pair (s, c) with |c| <= |s|: Fast2Sum.
+__device__ __forceinline__ FloatFloat ff_from_pair(float s, float c) {
+  const float hi = __fadd_rn(s, c);
+  return FloatFloat{hi, __fsub_rn(c, __fsub_rn(hi, s))};
+}
+
+__device__ __forceinline__ FloatFloat ff_add(FloatFloat a, FloatFloat b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bv = __fsub_rn(s, a.hi);
+  const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bv)), __fsub_rn(b.hi, bv));
+  const float lo = __fadd_rn(__fadd_rn(a.lo, b.lo), err);
+  return ff_from_pair(s, lo);
+}
+
+__device__ __forceinline__ double ff_to_double(FloatFloat a) {
+  return static_cast<double>(a.hi) + static_cast<double>(a.lo);
+}
+
+// ---------------------------------------------------------------------------
 // Programmatic dependent launch.  A kernel launched with the programmatic
 // stream serialization attribute may be scheduled while its predecessor on
 // the stream is still running; grid_dependency_wait() returns once the

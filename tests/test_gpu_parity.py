@@ -372,3 +372,19 @@ def test_gamma_weights_bit_exact(alpha):
                 assert np.array_equal(got, oracle.resample(w_h, B, 17, v))
             else:
                 assert np.array_equal(got[idx], oracle.resample_at(w_h, B, 17, idx, v))
+
+
+def test_huge_weights_are_reported_not_mistaken():
+    """Finite weights so large that a 4096-weight chunk's sum leaves the
+    binary32 range cannot give B on the device: the bound reports
+    MEGO_EWEIGHTS (and the resample writes nothing) instead of a wrong B;
+    large weights below that limit still match the oracle."""
+    n = 3 * 4096 + 5
+    w_h = np.full(n, 1e36, dtype=np.float32)
+    B_dev, status, _ = mego.mego_compute_B(_gpu(w_h), 0.01)
+    assert int(status.item()) == mego.MEGO_EWEIGHTS and int(B_dev.item()) == -1
+    w_h = (synthetic.gaussian_weights(n, 2.0, 5) * np.float32(1e30)).astype(np.float32)
+    B_dev, status, q_dev = mego.mego_compute_B(_gpu(w_h), 0.01)
+    st, B_cpu, q_cpu = oracle.compute_B(w_h, 0.01)
+    assert int(status.item()) == mego.MEGO_OK and _b_equal(int(B_dev.item()), B_cpu, q_cpu)
+    assert abs(float(q_dev.item()) - q_cpu) <= 1e-9 * max(1.0, q_cpu)
