@@ -202,3 +202,30 @@ def test_large_filters_take_six_chains_per_thread():
         batch.resample()
         torch.cuda.synchronize()
         assert all(torch.equal(a, d["anc"]) for a, d in zip(ref, filters)), (threads, ppt)
+
+
+@pytest.mark.parametrize("heavy_at", [0, 3, 6])
+def test_heaviest_filter_first_keeps_every_result(heavy_at):
+    """The queue hands the most expensive filter's work items out first; with
+    that filter first, in the middle or last in the plan (fixed B, so the
+    plan already knows it, then again after a bound), every filter's
+    ancestors still equal its single resample."""
+    ws = _make(7, 21, sizes=[300, 4097, 1000, 20000, 64, 9000, 33])
+    Bs = [5, 3, 7, 2, 9, 4, 6]
+    Bs[heavy_at] = 200
+    filters = [{"w": torch.from_numpy(w_h).to(DEV),
+                "anc": torch.empty(w_h.size, dtype=torch.int32, device=DEV),
+                "B": Bs[f], "stream_id": 90 + f} for f, w_h in enumerate(ws)]
+    batch = mego.Batch(filters, seed=SEED)
+    for with_bound in (False, True):
+        for d in filters:
+            d["anc"].fill_(-1)
+        if with_bound:
+            batch.bound(0.01)
+        batch.resample()
+        torch.cuda.synchronize()
+        for f, d in enumerate(filters):
+            alone = mego.mego_resample_gather(d["w"], Bs[f], None, SEED, d["stream_id"],
+                                              mego.MEGOPOLIS,
+                                              anc=torch.empty_like(d["anc"]))[0]
+            assert torch.equal(alone, d["anc"]), (heavy_at, with_bound, f)
