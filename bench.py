@@ -843,6 +843,7 @@ PROFILE_CASES = {
     "mego_smem_n2p14_y4": ("megopolis", 14, 4, "smem", None),
     "mego_global_n2p24_y4": ("megopolis", 24, 4, "global", None),
     "mego_gather6_n2p20_y2": ("megopolis", 20, 2, "global", "soa6"),
+    "mego_gather_aos4_n2p20_y2": ("megopolis", 20, 2, "global", "aos4"),
     "bound_n2p20": ("bound", 20, 2, None, None),
     "batch512": ("batch", 0, 0, None, None),
     "batch_sweep5": ("batch5", 20, 0, None, None),
@@ -891,9 +892,14 @@ def run_case(name: str):
     B = int(B_dev.item())
     anc = torch.empty(n, dtype=torch.int32, device=dev)
     x = x_out = None
+    layout = mego.LAYOUT_SOA
     if gather == "soa6":
         x = torch.from_numpy(synthetic.gaussian_state(n, 6, SEED)).to(dev)
         x_out = torch.empty_like(x)
+    elif gather == "aos4":
+        x = torch.from_numpy(synthetic.gaussian_state(n, 4, SEED).T.copy()).to(dev)
+        x_out = torch.empty_like(x)
+        layout = mego.LAYOUT_AOS4
     for _ in range(4):
         if kind == "bound":
             mego.mego_compute_B(w, EPS, B_dev=B_dev, status=status)
@@ -901,7 +907,7 @@ def run_case(name: str):
             variant = mego.MEGOPOLIS if kind == "megopolis" else mego.METROPOLIS
             cfg = {"path": mego.PATH_SMEM if path == "smem" else mego.PATH_GLOBAL}
             mego.mego_resample_gather(w, B, None, SEED, 0, variant, x_in=x, x_out=x_out,
-                                      anc=anc, cfg=cfg)
+                                      layout=layout, anc=anc, cfg=cfg)
     torch.cuda.synchronize()
     print(json.dumps({"case": name, "n": n, "B": B}))
 
