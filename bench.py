@@ -96,16 +96,17 @@ def _kernel_hash() -> str:
 
 
 def _profiled_traffic():
-    """DRAM bytes per launch of the Megopolis kernel from the committed ncu
-    summary, if it was taken on the current kernel source; else None."""
+    """(DRAM bytes per launch, kernel source hash) of the Megopolis kernel
+    from the committed ncu summary; the bytes are None unless the summary was
+    taken on the current kernel source."""
     try:
         text = open(PROFILE_TRAFFIC).read()
     except OSError:
-        return None
+        return None, None
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)\s*\(kernel source ([0-9a-f]+)\)", text)
-    if not m or m.group(2) != _kernel_hash():
-        return None
-    return float(m.group(1))
+    if not m:
+        return None, None
+    return (float(m.group(1)) if m.group(2) == _kernel_hash() else None), m.group(2)
 
 
 class ClockSampler:
@@ -187,27 +188,61 @@ def _dist():
     return world, rank, local
 
 
+def _host_cpu():
+    """(logical cores, CPU model) of this host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    import platform
+    return os.cpu_count() or 1, "%s (%s)" % (model or "unknown", platform.machine())
+
+
 def _cpu_baseline(sample_particles: int):
-    """The CPU oracle, single-threaded, on the first `sample_particles`
-    particles of each of the five weight vectors (Megopolis, same B)."""
+    """The CPU oracle on the first `sample_particles` particles of each of
+    the five weight vectors (Megopolis, same B): single-threaded (the
+    reported value), then the same sample split over every host core
+    ([i0, i1) ranges on host threads), labelled as threaded."""
     import oracle
     import synthetic
     oracle.build()
-    total_p = 0
-    t_total = 0.0
-    seeds = (SEED, SEED + 1)
-    for y in YS:
-        w = synthetic.gaussian_weights(N, y, SEED + y)
-        for seed in seeds:
-            t0 = time.perf_counter()
-            st, B, _ = oracle.compute_B(w, EPS)
-            oracle.resample(w, B, seed, oracle.MEGOPOLIS, i0=0, i1=sample_particles)
-            t_total += time.perf_counter() - t0
-            total_p += sample_particles
-    return {"value": total_p / t_total, "unit": UNIT, "cores": 1, "kind": "oracle",
+    cores, model = _host_cpu()
+    legs = {}
+    for threads in (1, cores):
+        total_p = 0
+        t_total = 0.0
+        for y in YS:
+            w = synthetic.gaussian_weights(N, y, SEED + y)
+            for seed in (SEED, SEED + 1):
+                t0 = time.perf_counter()
+                st, B, _ = oracle.compute_B(w, EPS)
+                oracle.resample(w, B, seed, oracle.MEGOPOLIS, i0=0, i1=sample_particles,
+                                threads=threads)
+                t_total += time.perf_counter() - t0
+                total_p += sample_particles
+        legs[threads] = (total_p / t_total, t_total)
+    return {"value": legs[1][0], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "host_cores": cores, "cpu_model": model,
             "sample": "first %d of %d particles for each y in 0..4 and 2 resampling "
                       "seeds (bound over all N, Megopolis chains for the sample); "
-                      "%.1f s of CPU work" % (sample_particles, N, t_total)}
+                      "%.1f s of CPU work on one core" % (sample_particles, N, legs[1][1]),
+            "threaded": {"value": legs[cores][0], "unit": UNIT, "cores": cores,
+                         "kind": "oracle split into [i0, i1) ranges over host threads",
+                         "seconds": legs[cores][1]}}
 
 
 def _batched_leg(args, mego, synthetic, torch, dev):
@@ -499,6 +534,7 @@ def run_reference(args):
                                "CPU oracle on the first %d particles per y" % sample,
                    "l2": "n/a (CPU)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "host_cores": _host_cpu()[0], "cpu_model": _host_cpu()[1],
                          "sample": "first %d of %d particles per y, %d steps"
                                    % (sample, N, args.steps)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -678,6 +714,7 @@ def run_gpu(args):
     pipe_peaks = _pipe_peaks(sms, clk_mhz)
     peak_gprop = min(pipe_peaks.values())
     achieved_gprop = N * sumB / (k_ms / 1e3) / 1e9
+    traffic_bytes, traffic_hash = _profiled_traffic()
     sink = torch.empty(4096, dtype=torch.float32, device=dev)
     probe_buf = torch.empty(32 << 20, dtype=torch.uint8, device=dev)
     mego.mego_probe_read(probe_buf, 16, sink, stream=stream)
@@ -801,21 +838,37 @@ def run_gpu(args):
                                    "Megopolis, gather into a new buffer",
                        "ms": statistics.median(fused),
                        "value": N / (statistics.median(fused) / 1e3), "unit": UNIT},
-        "roofline": {"bound": "alu", "achieved": achieved_gprop, "peak": peak_gprop,
-                     "unit": "Gproposals/s", "frac": achieved_gprop / peak_gprop,
-                     "traffic": _profiled_traffic(),
+        # Roofline of the dominant kernel against the memory level its
+        # weights live in: at N = 2^20 each vector (4 MiB) stays in L2 for the
+        # whole launch, so the peak is this run's L2 read probe.  The same
+        # bytes against HBM, and the proposal rate against the SM's
+        # arithmetic pipes (which bind first, see "units"), ride along.
+        "roofline": {"bound": "l2", "achieved": achieved_gbs, "peak": l2_best, "unit": "GB/s",
+                     "frac": achieved_gbs / l2_best,
+                     "peak_source": "measured: this run's L2 read probe (mego_probe_read, "
+                                    "32 MiB read 128 times with 16-byte loads, best of 5)",
+                     "traffic": traffic_bytes,
+                     "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum per "
+                                        "launch from profiles/batch_resample_sweep5_n2p20.md "
+                                        "(kernel source %s; this build %s)"
+                                        % (traffic_hash, _kernel_hash())),
+                     "algorithmic_bytes_per_launch": alg_bytes,
+                     "algorithmic_bytes_rule": "N (4 sum(B) + 8 x 5): 4 B per proposal read, "
+                                               "4 B own weight + 4 B ancestor per particle",
                      "kernel": "batched Megopolis resample of the five vectors "
-                               "(N=2^20 each, B=%s), %.1f us/launch" % (Bs, 1e3 * k_ms),
-                     "peak_derivation": "lowest per-unit rate: %d SMs x 64 ALU-pipe lane-ops "
-                                        "per SM-cycle x %.0f MHz / %.1f ALU ops per proposal"
-                                        % (sms, clk_mhz, ALU_OPS_PER_PROPOSAL),
-                     "pipe_peaks_gproposals": pipe_peaks,
-                     "memory_view": {"algorithmic_bytes_per_launch": alg_bytes,
-                                     "achieved_gbs": achieved_gbs,
-                                     "hbm_peak_gbs": hbm_peak, "hbm_peak_source": peak_src,
-                                     "frac_of_hbm": achieved_gbs / hbm_peak,
-                                     "l2_probe_gbs": l2_best,
-                                     "frac_of_l2_probe": achieved_gbs / l2_best}},
+                               "(N=2^20 each, B=%s), %.1f us/launch (CUDA events)"
+                               % (Bs, 1e3 * k_ms),
+                     "hbm_view": {"peak_gbs": hbm_peak,
+                                  "peak_source": "%s (MEASURED_PEAKS.json copy probe)" % peak_src,
+                                  "frac": achieved_gbs / hbm_peak},
+                     "units": {"achieved_gproposals": achieved_gprop,
+                               "peak_gproposals": pipe_peaks,
+                               "frac": {k: achieved_gprop / v for k, v in pipe_peaks.items()},
+                               "derivation": "per SM-cycle: 64 ALU-pipe lane-ops / %.1f ALU ops "
+                                             "per proposal; 32 wide multiplies / %.1f; 128 "
+                                             "issue slots / %.1f instructions; %d SMs at %.0f MHz"
+                                             % (ALU_OPS_PER_PROPOSAL, MULS_PER_PROPOSAL,
+                                                INSTR_PER_PROPOSAL, sms, clk_mhz)}},
         "batched": batched,
         "serving": serving,
         "sir_filter": sir,
@@ -839,6 +892,8 @@ def run_gpu(args):
 PROFILE_CASES = {
     # name: (variant, log2 N, y, path, gather)
     "mego_global_n2p20_y4": ("megopolis", 20, 4, "global", None),
+    "mego_global_n2p20_y0": ("megopolis", 20, 0, "global", None),
+    "mego_global_n2p20_y2": ("megopolis", 20, 2, "global", None),
     "metro_global_n2p20_y4": ("metropolis", 20, 4, "global", None),
     "mego_smem_n2p14_y4": ("megopolis", 14, 4, "smem", None),
     "mego_global_n2p24_y4": ("megopolis", 24, 4, "global", None),

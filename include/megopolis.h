@@ -163,15 +163,19 @@ mego_status mego_compute_B(const float* d_w, int32_t n, double eps,
  * or a real-time loop that must not call the allocator once it is running
  * (cudaMalloc may synchronise the device and takes unbounded time).  The
  * paper has no counterpart; this is a library convenience.
- * Same inputs, outputs and device-side status as mego_compute_B.  The
- * reduction's partial results go to a fixed 8 KiB array inside the library
- * (512 partials; every GPU that loads the library keeps it until exit).
+ * Same inputs, outputs and device-side status as mego_compute_B, and the
+ * same values bit for bit: the reduction runs the same grid and adds the
+ * same partials in the same order.  Its partial results go to a fixed
+ * 16 KiB array inside the library (1024 partials, the most the reduction
+ * grid ever uses; every GPU that loads the library keeps it until exit).
  * The first call on a device looks up that array's device address, so make
- * that first call before any stream capture.  All calls share the array:
+ * that first call before any stream capture; resetting the device
+ * (cudaDeviceReset) while the library is loaded is not supported, since the
+ * address is kept for the life of the process.  All calls share the array:
  * calls whose work overlaps on the GPU (other streams, other threads) race
  * and may return a wrong B; order them on one stream.  Nothing in the array
  * needs to start at zero.  n above MEGO_N_MAX is rejected with MEGO_EINVAL;
- * any n up to it fits, since the reduction never uses more than 512 CTAs.
+ * any n up to it fits.
  */
 mego_status mego_compute_B_noalloc(const float* d_w, int32_t n, double eps,
                                    int32_t b_max, int32_t* d_B,
@@ -315,7 +319,10 @@ typedef struct mego_request {
 
 typedef struct mego_completion {
   uint64_t id;
-  int32_t status;       /* MEGO_OK, or the error that failed the batch        */
+  int32_t status;       /* MEGO_OK; MEGO_EWEIGHTS when the bound rejected this
+                           request's weights (B = -1: no resample ran for it
+                           and its output buffers hold no result); or the
+                           error that failed the batch                        */
   int32_t n;
   int64_t latency_ns;   /* from submission to the results being on the host   */
   int32_t B;            /* iterations the bound gave this request (Eq. 3), or
@@ -417,6 +424,17 @@ mego_status mego_autotune(const float* d_w, int32_t n, int32_t B, int variant,
  * (0: none), and the record is cleared.  Synchronises the device.
  */
 mego_status mego_device_fault(int32_t* h_fault);
+
+/* Diagnostics (not part of the method): the number of polls the
+ * shared-memory path's first staging wait makes before it gives up, for
+ * resample calls queued after this one (host-wide setting).  polls < 0
+ * restores the default, 2^21 polls with back-off (about two seconds); a
+ * budget of 0 makes every staging wait expire at once, so a test can check
+ * the fault report without a fault: the CTA records fault 1, still waits
+ * with the full budget for its own copy to land, and writes nothing.
+ * polls above the default: MEGO_EINVAL.
+ */
+mego_status mego_set_stage_poll_budget(int64_t polls);
 
 /* ----------------------------------------------------------------------
  * Measurement helper (not part of the method): read `bytes` of d_buf

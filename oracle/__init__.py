@@ -165,19 +165,48 @@ def megopolis_index(i: int, o: int, n: int) -> int:
 # Resampling
 
 
+def host_threads() -> int:
+    """Host threads a split oracle run uses: every core of this machine."""
+    return max(1, os.cpu_count() or 1)
+
+
 def resample(w, B: int, seed: int, variant: int = MEGOPOLIS, stream_id: int = 0,
-             i0: int = 0, i1: int | None = None, psize_bytes: int = 0) -> np.ndarray:
-    """Ancestors of particles [i0, i1) (default: all) as int32."""
+             i0: int = 0, i1: int | None = None, psize_bytes: int = 0,
+             threads: int = 1) -> np.ndarray:
+    """Ancestors of particles [i0, i1) (default: all) as int32.
+
+    threads > 1 splits [i0, i1) into contiguous sub-ranges and runs the
+    single-threaded C oracle on each from a pool of host threads (ctypes
+    releases the interpreter lock during the call).  Every particle's chain
+    depends only on (w, B, seed, stream id, its own index), so the result is
+    the same array as the single-threaded run; only the wall time changes.
+    """
     lib = _load()
     w = _f32(w)
     n = w.shape[0]
     if i1 is None:
         i1 = n
     out = np.empty(max(i1 - i0, 0), dtype=np.int32)
-    st = lib.oracle_resample(_ptr(w), n, int(B), int(seed), int(stream_id),
-                             int(variant), int(psize_bytes), int(i0), int(i1),
-                             _ptr(out))
-    _check(st, "oracle_resample")
+    if threads <= 1 or i1 - i0 < 4096:
+        st = lib.oracle_resample(_ptr(w), n, int(B), int(seed), int(stream_id),
+                                 int(variant), int(psize_bytes), int(i0), int(i1),
+                                 _ptr(out))
+        _check(st, "oracle_resample")
+        return out
+    # Four ranges per thread, so that uneven per-range times still balance.
+    pieces = min(4 * int(threads), (i1 - i0) // 1024)
+    cuts = [i0 + (i1 - i0) * k // pieces for k in range(pieces + 1)]
+
+    def one(k):
+        a, b = cuts[k], cuts[k + 1]
+        return lib.oracle_resample(_ptr(w), n, int(B), int(seed), int(stream_id),
+                                   int(variant), int(psize_bytes), a, b,
+                                   _ptr(out) + 4 * (a - i0))
+
+    import concurrent.futures as cf
+    with cf.ThreadPoolExecutor(max_workers=int(threads)) as ex:
+        for st in ex.map(one, range(pieces)):
+            _check(st, "oracle_resample")
     return out
 
 

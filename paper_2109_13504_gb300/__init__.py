@@ -134,6 +134,7 @@ def _load():
         "mego_sync_status": ([vp, vp, f64, vp], ci),
         "mego_probe_read": ([vp, sz, i32, vp, vp], ci),
         "mego_device_fault": ([vp], ci),
+        "mego_set_stage_poll_budget": ([ctypes.c_int64], ci),
         "mego_batch_plan_bytes": ([ctypes.POINTER(Filter), i32], sz),
         "mego_batch_plan": ([ctypes.POINTER(Filter), i32, ci, ci, u64, vp, sz,
                              ctypes.POINTER(BatchHandle), vp], ci),
@@ -420,6 +421,12 @@ def mego_device_fault() -> int:
     h = ctypes.c_int32(-1)
     _check(_load().mego_device_fault(ctypes.addressof(h)), "mego_device_fault")
     return int(h.value)
+
+
+def mego_set_stage_poll_budget(polls: int) -> None:
+    """Polls of the shared-memory staging wait before it reports a fault
+    (diagnostics; polls < 0 restores the default)."""
+    _check(_load().mego_set_stage_poll_budget(int(polls)), "mego_set_stage_poll_budget")
 
 
 def mego_probe_read(buf: torch.Tensor, reps: int, sink: torch.Tensor, stream=None) -> None:

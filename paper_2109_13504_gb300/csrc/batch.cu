@@ -383,6 +383,7 @@ __global__ void __launch_bounds__(max_threads_for(P)) batch_resample_kernel(cons
     p.dim = d.dim;
     p.nw = 1u;
     p.npart = d.n;
+    p.stage_polls = kMaxPolls;
     p.S = stream_key(a.K, d.sid);
     const uint32_t seg_lo = local * item_segs;
     const uint32_t seg_hi = min(p.nseg, seg_lo + item_segs);

@@ -22,6 +22,9 @@
 namespace {
 
 std::atomic<uint64_t> g_launches{0};
+// Poll budget of the shared-memory path's first staging wait (diagnostics:
+// mego_set_stage_poll_budget).
+std::atomic<uint32_t> g_stage_polls{mego::kMaxPolls};
 
 struct DevInfo {
   int sms = 0;
@@ -335,6 +338,7 @@ mego_status mego_resample_gather(const float* d_w, int32_t n, int32_t B, const i
   a.p.dim = dim;
   a.p.nw = nw;
   a.p.npart = npart;
+  a.p.stage_polls = g_stage_polls.load();
   a.K = mego::make_round_keys(seed);
   a.p.S = mego::make_stream_key(a.K, stream_id);
   a.B_dev = d_B;
@@ -366,7 +370,8 @@ static mego_status bound_common(const float* src, int32_t n, bool likelihood, fl
   if (ws_bytes < mego_workspace_bytes(n)) return MEGO_ENOMEM;
   if (reinterpret_cast<uintptr_t>(d_ws) & 255u) return MEGO_EINVAL;
   const uint32_t un = static_cast<uint32_t>(n);
-  if (likelihood && overlaps(src, un * 4u, d_w, un * 4u)) return MEGO_EINVAL;
+  const size_t v_bytes = static_cast<size_t>(un) * 4u;  // up to 4 GiB: size_t, not 32 bits
+  if (likelihood && overlaps(src, v_bytes, d_w, v_bytes)) return MEGO_EINVAL;
   auto* parts = static_cast<mego::Partial*>(d_ws);
   const int grid = mego::reduce_grid(un);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -550,6 +555,12 @@ mego_status mego_device_fault(int32_t* h_fault) {
     if (v && cudaMemset(w, 0, sizeof v) != cudaSuccess) return MEGO_ECUDA;
   }
   *h_fault = any;
+  return MEGO_OK;
+}
+
+mego_status mego_set_stage_poll_budget(int64_t polls) {
+  if (polls > static_cast<int64_t>(mego::kMaxPolls)) return MEGO_EINVAL;
+  g_stage_polls.store(polls < 0 ? mego::kMaxPolls : static_cast<uint32_t>(polls));
   return MEGO_OK;
 }
 

@@ -5,7 +5,8 @@
 // this file (every GPU that loads the library holds it until the process
 // exits).  Host code cannot use the array's name as a device address, so the
 // first call on each device looks the address up with cudaGetSymbolAddress
-// while that device is current, and later calls reuse it.
+// while that device is current, and later calls reuse it (for the life of
+// the process: a device reset while the library is loaded is unsupported).
 #include <cstdint>
 #include <mutex>
 
@@ -16,9 +17,11 @@
 
 namespace {
 
-// Capacity of the fixed scratch: this many per-CTA partials (16 bytes each,
-// 8 KiB in all).  The reduction grid is capped at this many CTAs.
-constexpr int kNoAllocParts = 512;
+// Capacity of the fixed scratch: one per-CTA partial (16 bytes) for every
+// CTA the reduction grid can have, 16 KiB in all.  The grid is then the one
+// mego_compute_B uses, so both add the same partials in the same order.
+constexpr int kNoAllocParts = mego::kMaxParts;
+static_assert(kNoAllocParts * sizeof(mego::Partial) == 16384, "16 KiB of partials");
 
 static __device__ __align__(256) mego::Partial g_noalloc_parts[kNoAllocParts];
 
@@ -55,8 +58,8 @@ extern "C" mego_status mego_compute_B_noalloc(const float* d_w, int32_t n, doubl
   if (!(eps > 0.0 && eps <= 1.0)) return MEGO_EINVAL;
   if (b_max < 1 || b_max > MEGO_B_MAX) return MEGO_EINVAL;
   const uint32_t un = static_cast<uint32_t>(n);
-  int grid = mego::reduce_grid(un);
-  if (grid > kNoAllocParts) grid = kNoAllocParts;
+  const int grid = mego::reduce_grid(un);  // at most mego::kMaxParts CTAs
+  if (grid > kNoAllocParts) return MEGO_EINVAL;
   mego::Partial* parts = nullptr;
   const mego_status s = scratch_for_current_device(&parts);
   if (s != MEGO_OK) return s;

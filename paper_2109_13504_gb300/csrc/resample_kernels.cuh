@@ -34,6 +34,7 @@ struct Problem {
   int32_t dim;
   uint32_t nw;           // C1/C2: weights per partition
   uint32_t npart;        // C1/C2: number of partitions
+  uint32_t stage_polls;  // SMEM path: polls of the first staging wait
   StreamKey S;           // stream constants for (seed, stream id)
 };
 
@@ -82,7 +83,13 @@ __device__ __forceinline__ float ldw_at(const float* __restrict__ w, uint32_t x0
 }
 
 // Stage w[0, n) into dynamic shared memory.  Returns false (uniformly for the
-// CTA) if the bulk copy did not complete within the poll budget.
+// CTA) if the bulk copy did not complete within the poll budget
+// a.stage_polls (kMaxPolls by default, about two seconds of polling with
+// back-off); the CTA then records the fault and waits again, with the full
+// budget, for the copies it issued to land before it leaves, so no copy
+// writes into shared memory that the SM has handed to another CTA.  (Should
+// that second wait also expire, the memory system itself has stopped; the
+// CTA leaves with the fault recorded.)
 __device__ __forceinline__ bool stage_weights(const Problem& a) {
   __shared__ __align__(8) uint64_t bar;
   float* s_w = reinterpret_cast<float*>(g_dyn_smem);
@@ -104,7 +111,7 @@ __device__ __forceinline__ bool stage_weights(const Problem& a) {
                reinterpret_cast<const char*>(a.w) + off, len, &bar);
     }
   }
-  const bool done = mbar_wait_bounded(&bar, 0u, kMaxPolls);
+  const bool done = mbar_wait_bounded(&bar, 0u, a.stage_polls);
   if (__syncthreads_and(done ? 1 : 0)) return true;
   if (threadIdx.x == 0) {
     if (a.fault) atomicExch(a.fault, kFaultStageTimeout);

@@ -253,7 +253,9 @@ void mego_server::finish(InFlight& f) {
     const Req& q = f.reqs[k];
     mego_completion c{};
     c.id = q.r.id;
-    c.status = MEGO_OK;
+    // B < 0: the bound rejected this request's weights (NaN, Inf, negative,
+    // all zero, or B above its cap) and the resample wrote nothing for it.
+    c.status = Bs[k] >= 0 ? MEGO_OK : MEGO_EWEIGHTS;
     c.latency_ns = t - q.t_submit;
     c.n = q.r.n;
     c.B = Bs[k];

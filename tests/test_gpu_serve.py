@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import synthetic
 
 pytestmark = pytest.mark.gpu
@@ -104,3 +105,68 @@ def test_copied_buffers_match_direct_ones(mode):
         a_ref, x_ref, _ = _alone(w.numpy(), x.numpy(), rid)
         assert np.array_equal(anc.numpy(), a_ref), rid
         assert np.array_equal(x_out.numpy(), x_ref), rid
+
+
+def test_served_results_equal_the_oracle_up_to_2p20():
+    """Requests shaped like the serving workload (N = floor(2^U[10,20]),
+    Eq. 12 weights with y = 2, 4-dim AoS state), served in a mix under a
+    budget that holds several at once: every ancestor and every gathered
+    state row equals the CPU oracle's (Algorithm 5 with the request's id as
+    stream id, then the gather), and each completion reports the oracle's B.
+    The largest request is 2^20 particles."""
+    t, reqs = _requests(14, 11, 10.0, 20.0)
+    n = 1 << 20
+    w = torch.from_numpy(synthetic.gaussian_weights(n, 2.0, 999)).pin_memory()
+    x = torch.from_numpy(np.ascontiguousarray(synthetic.gaussian_state(n, 4, 998).T)).pin_memory()
+    reqs.append((5000, w, x, torch.full((n,), -1, dtype=torch.int32).pin_memory(),
+                 torch.zeros((n, 4), dtype=torch.float32).pin_memory()))
+    t = list(t) + [float(t[-1])]
+    server = mego.Server(arena_bytes=3 * 40 * n + (8 << 20), seed=SEED, max_batch=8)
+    server.replay(reqs, t)
+    done = {c[0]: c for c in server.poll()}
+    server.close()
+    assert len(done) == len(reqs)
+    threads = oracle.host_threads()
+    for rid, w, x, anc, x_out in reqs:
+        c = done[rid]
+        assert c[1] == mego.MEGO_OK, rid
+        w_h = w.numpy()
+        st, B_ref, q_ref = oracle.compute_B(w_h, 0.01)
+        assert st == oracle.OK
+        assert c[4] == B_ref or (abs(q_ref - round(q_ref)) <= 1e-9 * max(1.0, q_ref)
+                                 and abs(c[4] - B_ref) <= 1), (rid, c[4], B_ref)
+        ref = oracle.resample(w_h, c[4], SEED, oracle.MEGOPOLIS, stream_id=rid & 0xFFFFFFFF,
+                              threads=threads)
+        assert np.array_equal(anc.numpy(), ref), rid
+        assert np.array_equal(x_out.numpy(), oracle.gather_aos4(x.numpy(), ref)), rid
+
+
+def test_request_with_invalid_weights_completes_with_an_error():
+    """A request whose weights the bound rejects (a NaN, or all zero)
+    completes with MEGO_EWEIGHTS and B = -1; its output buffers are left as
+    they were, and the requests batched with it are served normally."""
+    t, reqs = _requests(6, 12, 8.0, 12.0)
+    bad = []
+    for k, fill in enumerate((float("nan"), 0.0)):
+        rid, w, x, anc, x_out = reqs[2 * k + 1]
+        if fill == fill:
+            w.fill_(fill)
+        else:
+            w[w.numel() // 2] = fill
+        bad.append(rid)
+    server = mego.Server(arena_bytes=256 << 20, seed=SEED, max_batch=8)
+    for r in reqs:
+        server.submit(*r)
+    server.drain(60.0)
+    done = {c[0]: c for c in server.poll()}
+    server.close()
+    assert len(done) == len(reqs)
+    for rid, w, x, anc, x_out in reqs:
+        c = done[rid]
+        if rid in bad:
+            assert c[1] == mego.MEGO_EWEIGHTS and c[4] == -1, c
+            assert (anc.numpy() == -1).all() and (x_out.numpy() == 0).all()
+        else:
+            assert c[1] == mego.MEGO_OK, c
+            a_ref, x_ref, B_ref = _alone(w.numpy(), x.numpy(), rid)
+            assert np.array_equal(anc.numpy(), a_ref) and np.array_equal(x_out.numpy(), x_ref)

@@ -56,6 +56,20 @@ def test_subrange_matches_full_run(variant):
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
+def test_host_thread_split_matches_single_thread(variant):
+    # The split run that checks full-size GPU results uses many contiguous
+    # [i0, i1) ranges on host threads; it must give the single-threaded array.
+    n = 50_000 + 13
+    w = synthetic.gaussian_weights(n, 3.0, 8)
+    full = oracle.resample(w, 21, 6, variant, stream_id=4)
+    for threads in (2, 3, 8):
+        assert np.array_equal(oracle.resample(w, 21, 6, variant, stream_id=4,
+                                              threads=threads), full)
+    sub = oracle.resample(w, 21, 6, variant, stream_id=4, i0=777, i1=n - 5, threads=5)
+    assert np.array_equal(sub, full[777:n - 5])
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("n,B", [(16, 5), (100, 40), (1024, 300)])
 def test_single_heavy_particle_absorption_rate(variant, n, B):
     p = n // 3

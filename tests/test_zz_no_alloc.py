@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import synthetic
 
 pytestmark = pytest.mark.gpu
@@ -35,12 +36,25 @@ def _without_allocation(w, B_dev, status, q):
 
 
 def _same(a, b):
+    # Both entry points run the same reduction grid and add the same
+    # partials in the same order: B, status and q are identical, bit for bit.
     B1, s1, q1 = a
     B2, s2, q2 = b
     assert s1 == s2 == mego.MEGO_OK
-    assert abs(q1 - q2) <= 1e-9 * max(1.0, abs(q1))
-    if B1 != B2:      # only a value before the ceiling within 1e-9 of an integer
-        assert abs(q1 - round(q1)) <= 1e-9 * max(1.0, abs(q1)) and abs(B1 - B2) <= 1
+    assert B1 == B2
+    assert q1 == q2
+
+
+def _matches_oracle(w_h, got):
+    # The oracle's bound (Eq. 3, sum in double in index order) equals the
+    # device's unless the value before the ceiling lies within 1e-9 of an
+    # integer, where the two summation orders may round to either side.
+    B, _, q = got
+    st, B_ref, q_ref = oracle.compute_B(w_h, 0.01)
+    assert st == oracle.OK
+    assert abs(q - q_ref) <= 1e-9 * max(1.0, abs(q_ref))
+    if B != B_ref:
+        assert abs(q_ref - round(q_ref)) <= 1e-9 * max(1.0, abs(q_ref)) and abs(B - B_ref) <= 1
 
 
 def test_noalloc_bound_matches_workspace_bound_two_calls_in_a_row():
@@ -48,11 +62,16 @@ def test_noalloc_bound_matches_workspace_bound_two_calls_in_a_row():
     status = torch.full((1,), -9, dtype=torch.int32, device=DEV)
     q = torch.zeros(1, dtype=torch.float64, device=DEV)
     # Two calls in a row on different inputs (the second one larger, so it
-    # uses more of the shared scratch than the first), then the first again.
-    cases = [(1 << 16, 3.0, 1), ((1 << 21) + 77, 1.0, 2), (1 << 16, 3.0, 1)]
+    # fills all 1024 partials of the shared scratch where the first used
+    # 16), then the first again; the largest case runs the widest grid.
+    cases = [(1 << 16, 3.0, 1), ((1 << 21) + 77, 1.0, 2), (1 << 16, 3.0, 1),
+             ((1 << 24) + 5, 4.0, 3)]
     for n, y, seed in cases:
-        w = torch.from_numpy(synthetic.gaussian_weights(n, y, seed)).to(DEV)
-        _same(_with_workspace(w), _without_allocation(w, B_dev, status, q))
+        w_h = synthetic.gaussian_weights(n, y, seed)
+        w = torch.from_numpy(w_h).to(DEV)
+        got = _without_allocation(w, B_dev, status, q)
+        _same(_with_workspace(w), got)
+        _matches_oracle(w_h, got)
 
 
 def test_noalloc_bound_reports_bad_weights_and_arguments():
