@@ -348,7 +348,8 @@ __global__ void __launch_bounds__(256) batch_finalize_kernel(const __grid_consta
 // Persistent resample over the work queue.
 
 template <int VARIANT, int P, int GATHER>
-__global__ void __launch_bounds__(max_threads_for(P)) batch_resample_kernel(const __grid_constant__ BatchArgs a) {
+__global__ void __launch_bounds__(max_threads_for(P))
+batch_resample_kernel(const __grid_constant__ BatchArgs a) {
   __shared__ int2 s_win[kMaxWarps][32];
   PlanHeader* h = reinterpret_cast<PlanHeader*>(a.plan);
   const FilterDev* F = reinterpret_cast<const FilterDev*>(a.plan + a.off_filters);
@@ -387,7 +388,11 @@ __global__ void __launch_bounds__(max_threads_for(P)) batch_resample_kernel(cons
     p.S = stream_key(a.K, d.sid);
     const uint32_t seg_lo = local * item_segs;
     const uint32_t seg_hi = min(p.nseg, seg_lo + item_segs);
-    run_segments<VARIANT, P, false, GATHER>(p, a.K, B, seg_lo, seg_hi, lane, win);
+    // Items are single batches, so the short-chain path (which saves the
+    // offset draws of a warp's later batches) has nothing to save here; the
+    // general path keeps the kernel's register allocation free of it.
+    OffsetWindow ow{0u, false};
+    run_segments<VARIANT, P, false, GATHER, false>(p, a.K, B, seg_lo, seg_hi, lane, win, ow);
   }
   // The last warp out resets the queue for the next launch of this plan.
   if (lane == 0) {

@@ -55,6 +55,13 @@ constexpr int kMaxWarps = 8;
 // the compiler use them and still fit three CTAs per SM.
 constexpr int max_threads_for(int P) { return P == 6 ? 128 : 256; }
 
+// Resident CTAs per SM the single-resample kernel's register allocation must
+// allow (the second __launch_bounds__ argument): three for six chains per
+// thread (up to 168 registers), pinned so that the short-chain path added to
+// the kernel cannot move the allocation of the long-chain loop; measured
+// faster than four CTAs of 128 registers on 2^20 weights at B = 356.
+constexpr int min_ctas_single(int P) { return P == 6 ? 3 : 1; }
+
 extern __shared__ float4 g_dyn_smem[];
 
 constexpr uint32_t kStageChunk = 32768u;
@@ -165,6 +172,19 @@ __device__ __forceinline__ uint32_t wrap_index(uint32_t j, uint32_t n) {
   if (j >= n) j -= n;
   if (j >= n) j %= n;
   return j;
+}
+
+// The same reduction for the short-chain path, where the choice is made once
+// per launch: a batch forms indices j < n + 32 P (a column is below n + 32
+// and a batch adds at most 32 (P - 1)), so for n >= 32 P one conditional
+// subtraction suffices (SMALL = false) and only n < 32 P needs the division.
+template <bool SMALL>
+__device__ __forceinline__ uint32_t wrap_small(uint32_t j, uint32_t n) {
+  if constexpr (SMALL) {
+    return j % n;
+  } else {
+    return j >= n ? j - n : j;
+  }
 }
 
 // Loads of one Megopolis iteration for the P segments of a batch when the
@@ -281,6 +301,97 @@ __device__ __forceinline__ void megopolis_batch(const Problem& a, const RoundKey
   uint32_t k[P];
 #pragma unroll
   for (int p = 0; p < P; ++p) k[p] = wrap_index(kx[p] + 32u * p, n);
+  finish_batch<P, GATHER>(a, ibase, k, live);
+}
+
+// ---------------------------------------------------------------------------
+// Megopolis for short chains, B <= kShortB (the first 30 iterations fit one
+// offset table, so it is filled once per batch and never refilled).  The
+// offsets depend only on (seed, stream, b, n), not on the batch: each lane
+// keeps o^(lane) in a register (OffsetWindow) for all the batches a warp runs
+// on one problem, so only the first batch runs the generator for them; a
+// later batch recomputes just the bases.  Loads take the immediate-offset
+// path whenever none of the iterations' partitions runs past n, the tail
+// group included, and the index reduction modulo n is chosen per launch
+// (wrap_small).  Same results as megopolis_batch, bit for bit.
+constexpr int kShortB = 30;
+
+struct OffsetWindow {
+  uint32_t o;   // o^(lane) of the first window (iterations 0..31)
+  bool valid;
+};
+
+template <int P, bool SMEM, int GATHER, bool SMALL>
+__device__ __forceinline__ void megopolis_short(const Problem& a, const RoundKeys& K, int B,
+                                                uint32_t s0, uint32_t seg_hi,
+                                                uint32_t lane, int2* win, OffsetWindow& ow) {
+  const uint32_t n = a.n;
+  const uint32_t ibase = s0 * 32u + lane;
+  float wk[P];
+  uint32_t kx[P];
+  bool live[P];
+  PhiloxLane ph[P];
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    const uint32_t i = ibase + 32u * p;
+    live[p] = (s0 + p < seg_hi) && (i < n);
+    wk[p] = ldw<SMEM>(a.w, i < n ? i : n - 1u);
+    kx[p] = ibase;
+    ph[p].init(i, kTagMegoU, K, a.S);
+  }
+  if (!ow.valid) {  // warp-uniform
+    ow.o = mego_offset(K, a.S, lane, n);
+    ow.valid = true;
+  }
+  const uint32_t o = ow.o;
+  uint32_t base = s0 * 32u + (o & ~31u);
+  base = base >= n ? base - n : base;
+  const uint32_t fast_mask = __ballot_sync(0xFFFFFFFFu, base + 32u * P <= n);
+  __syncwarp();
+  win[lane] = make_int2(static_cast<int>(base), static_cast<int>(o));
+  __syncwarp();
+  constexpr int U = kMegoPerCall;
+  uint32_t g = 0u;
+  for (int b0 = 0; b0 < B; b0 += U, ++g) {
+    uint32_t mh, ml;
+    PhiloxLane::group(g, a.S, mh, ml);
+    const int nb = B - b0 < U ? B - b0 : U;
+    const uint32_t need = (1u << nb) - 1u;
+    const bool fast = ((fast_mask >> b0) & need) == need;
+    float wj[U][P];
+    uint32_t x0[U];
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      if (q < nb) {
+        x0[q] = mego_column(win[b0 + q], lane);
+        if (fast) {
+#pragma unroll
+          for (int p = 0; p < P; ++p) wj[q][p] = ldw_at<SMEM>(a.w, x0[q], 32u * p);
+        } else {
+#pragma unroll
+          for (int p = 0; p < P; ++p)
+            wj[q][p] = ldw<SMEM>(a.w, wrap_small<SMALL>(x0[q] + 32u * p, n));
+        }
+      }
+    }
+    uint4 r[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) r[p] = ph[p].gen(mh, ml, K);
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      if (q < nb) {
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+          const bool acc = accept(u_of(mego_word(r[p], q)), wk[p], wj[q][p]);
+          wk[p] = acc ? wj[q][p] : wk[p];
+          kx[p] = acc ? x0[q] : kx[p];
+        }
+      }
+    }
+  }
+  uint32_t k[P];
+#pragma unroll
+  for (int p = 0; p < P; ++p) k[p] = wrap_small<SMALL>(kx[p] + 32u * p, n);
   finish_batch<P, GATHER>(a, ibase, k, live);
 }
 
@@ -418,14 +529,28 @@ __device__ __forceinline__ void partition_batch(const Problem& a, const RoundKey
 
 // ---------------------------------------------------------------------------
 // The chains of whole batches [seg_lo, seg_hi) of one problem for one warp.
-template <int VARIANT, int P, bool SMEM, int GATHER>
+template <int VARIANT, int P, bool SMEM, int GATHER, bool SHORT = true>
 __device__ __forceinline__ void run_segments(const Problem& a, const RoundKeys& K, int B,
                                              uint32_t seg_lo, uint32_t seg_hi, uint32_t lane,
-                                             int2* win) {
+                                             int2* win, OffsetWindow& ow) {
+  if constexpr (VARIANT == kMegopolis) {
+    if (SHORT && B <= kShortB) {  // uniform for the problem
+      // n < 32 P: a batch's indices may pass 2n and need the division.
+      if (a.n < 32u * P) {
+        for (uint32_t s0 = seg_lo; s0 < seg_hi; s0 += P)
+          megopolis_short<P, SMEM, GATHER, true>(a, K, B, s0, seg_hi, lane, win, ow);
+      } else {
+        for (uint32_t s0 = seg_lo; s0 < seg_hi; s0 += P)
+          megopolis_short<P, SMEM, GATHER, false>(a, K, B, s0, seg_hi, lane, win, ow);
+      }
+    } else {
+      for (uint32_t s0 = seg_lo; s0 < seg_hi; s0 += P)
+        megopolis_batch<P, SMEM, GATHER>(a, K, B, s0, seg_hi, lane, win);
+    }
+    return;
+  }
   for (uint32_t s0 = seg_lo; s0 < seg_hi; s0 += P) {
-    if constexpr (VARIANT == kMegopolis) {
-      megopolis_batch<P, SMEM, GATHER>(a, K, B, s0, seg_hi, lane, win);
-    } else if constexpr (VARIANT == kMetropolis) {
+    if constexpr (VARIANT == kMetropolis) {
       metropolis_batch<P, SMEM, GATHER>(a, K, B, s0, seg_hi, lane);
     } else {
       partition_batch<VARIANT, P, SMEM, GATHER>(a, K, B, s0, seg_hi, lane);
@@ -434,7 +559,8 @@ __device__ __forceinline__ void run_segments(const Problem& a, const RoundKeys& 
 }
 
 template <int VARIANT, int P, bool SMEM, int GATHER>
-__global__ void __launch_bounds__(max_threads_for(P)) resample_kernel(const __grid_constant__ ResampleArgs a) {
+__global__ void __launch_bounds__(max_threads_for(P), min_ctas_single(P))
+resample_kernel(const __grid_constant__ ResampleArgs a) {
   __shared__ int2 s_win[kMaxWarps][32];
   grid_dependency_wait();  // inputs (weights, a device-side B) written by the predecessor
   const int B = a.B_dev ? *a.B_dev : a.B;
@@ -451,8 +577,9 @@ __global__ void __launch_bounds__(max_threads_for(P)) resample_kernel(const __gr
   const uint32_t seg_lo = static_cast<uint32_t>(nbat * gw / tw) * P;
   uint32_t seg_hi = static_cast<uint32_t>(nbat * (gw + 1u) / tw) * P;
   if (seg_hi > a.p.nseg) seg_hi = a.p.nseg;
+  OffsetWindow ow{0u, false};
   run_segments<VARIANT, P, SMEM, GATHER>(a.p, a.K, B, seg_lo, seg_hi, lane,
-                                         s_win[threadIdx.x >> 5]);
+                                         s_win[threadIdx.x >> 5], ow);
 }
 
 // Host-side launcher for one variant (defined in resample_<variant>.cu).
