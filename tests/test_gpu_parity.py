@@ -233,6 +233,42 @@ def test_gather_soa_and_aos4(variant, n):
     assert np.array_equal(a_out.cpu().numpy(), oracle.gather_aos4(a_h, ref))
 
 
+def test_bound_workspace_reuse_garbage_and_graph_replay():
+    """The bound writes one partial per CTA into the caller's workspace and
+    folds them in a second launch.  A workspace full of arbitrary bytes,
+    calls of different grid sizes on the same workspace, and replays of a
+    captured graph whose input changes between replays must all give the
+    oracle's B."""
+    ws = torch.randint(0, 256, (mego.workspace_bytes(1 << 24),), dtype=torch.uint8,
+                       device=DEV)
+    cases = [((1 << 22) + 3, 2.0, 1), (5000, 4.0, 2), (1, 0.0, 3), ((1 << 22) + 3, 3.0, 4),
+             (70_000, 1.0, 5)]
+    for n, y, seed in cases:
+        w_h = synthetic.gaussian_weights(n, y, seed)
+        B_dev, status, q_dev = mego.mego_compute_B(_gpu(w_h), 0.01, ws=ws)
+        st, B_cpu, q_cpu = oracle.compute_B(w_h, 0.01)
+        assert mego.mego_sync_status(status) == mego.MEGO_OK
+        assert _b_equal(int(B_dev.item()), B_cpu, q_cpu), (n, y)
+        assert abs(float(q_dev.item()) - q_cpu) <= 1e-9 * max(1.0, q_cpu)
+    n = 300_001
+    w = torch.empty(n, dtype=torch.float32, device=DEV)
+    B_dev = torch.empty(1, dtype=torch.int32, device=DEV)
+    status = torch.empty(1, dtype=torch.int32, device=DEV)
+    q_dev = torch.empty(1, dtype=torch.float64, device=DEV)
+    side = torch.cuda.Stream(DEV)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        mego.mego_compute_B(w, 0.01, B_dev=B_dev, status=status, q=q_dev, ws=ws, stream=side)
+    for y in (0.0, 4.0, 2.0, 2.0):
+        w_h = synthetic.gaussian_weights(n, y, 7 + int(y))
+        w.copy_(torch.from_numpy(w_h))
+        g.replay()
+        torch.cuda.synchronize()
+        st, B_cpu, q_cpu = oracle.compute_B(w_h, 0.01)
+        assert int(status.item()) == mego.MEGO_OK
+        assert _b_equal(int(B_dev.item()), B_cpu, q_cpu), y
+
+
 def test_device_bound_path_equals_host_path():
     n = 1 << 18
     w_h = synthetic.gaussian_weights(n, 3.0, 9)
