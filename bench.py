@@ -295,6 +295,25 @@ def _batched_leg(args, mego, synthetic, torch, dev):
             if r >= args.warmup:
                 t_sep.append(a.elapsed_time(b))
         shape = batch.shape
+        # A/B of the shared-memory phase: each threshold with the tuned
+        # launch shape (filters of at most that many weights are resampled
+        # whole by one CTA each from shared memory).
+        smem_ab = {}
+        for thr in (0, 4096, 16384, 49152):
+            batch.close()                       # drop the graph before re-planning
+            batch.set_smem(thr, stream=side)
+            batch.capture(EPS, stream=side)
+            tt = []
+            for r in range(args.warmup + reps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(side)
+                batch.replay(stream=side)
+                b.record(side)
+                side.synchronize()
+                if r >= args.warmup:
+                    tt.append(a.elapsed_time(b))
+            smem_ab[str(thr)] = {"ms_p50": stats.median(tt),
+                                 "smem_filters": batch.shape["smem_filters"]}
         batch.close()
 
     def pct(v, p):
@@ -309,7 +328,8 @@ def _batched_leg(args, mego, synthetic, torch, dev):
             "separate_launches_ms_p50": pct(t_sep, 50),
             "separate_particles_per_s": total / (stats.median(t_sep) / 1e3),
             "speedup": stats.median(t_sep) / stats.median(t_graph),
-            "shape": shape}
+            "shape": shape,
+            "smem_threshold_ab": smem_ab}
 
 
 def _serving_leg(args, mego, synthetic, torch, dev):

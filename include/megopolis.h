@@ -42,7 +42,7 @@
 extern "C" {
 #endif
 
-#define MEGO_ABI_VERSION 3
+#define MEGO_ABI_VERSION 4
 #define MEGO_N_MAX (1 << 30)
 #define MEGO_B_MAX (1 << 24)
 
@@ -267,6 +267,17 @@ typedef struct mego_batch {
   int32_t grid;
   void* graph_exec;    /* captured graph, or NULL                             */
   int32_t graph_kernels; /* kernels in the captured graph                     */
+  /* Shared-memory phase (ABI 4): filters of at most smem_max_n weights are
+   * resampled whole by one CTA each, their weights staged once in shared
+   * memory, before the warp-level queue takes the other filters' items
+   * (0: no such phase).  Set by mego_batch_set_smem or mego_batch_autotune. */
+  int32_t smem_max_n;
+  int32_t smem_filters; /* filters in the shared-memory phase                 */
+  size_t smem_bytes;    /* dynamic shared memory per CTA of the launch        */
+  /* The caller's filter array given to mego_batch_plan; mego_batch_set_smem
+   * and mego_batch_autotune re-plan from it, so it must stay valid (and
+   * unchanged) while they may be called. */
+  const mego_filter* h_filters;
 } mego_batch;
 
 size_t mego_batch_plan_bytes(const mego_filter* h_filters, int32_t count);
@@ -284,8 +295,21 @@ mego_status mego_batch_resample(const mego_batch* b, void* stream);
  * is fixed in the plan, and the plan's default shape takes one item per warp
  * batch.  Any shape gives the same results. */
 mego_status mego_batch_set_shape(mego_batch* b, int32_t threads, int32_t ppt);
-/* Time every shape on the batch as planned (outputs are overwritten) and
- * keep the fastest. */
+/* Shared-memory phase threshold: re-plan (in the same plan buffer, on
+ * `stream`) so that filters of at most smem_max_n weights are resampled by
+ * one CTA each from shared memory.  0 turns the phase off; the maximum is
+ * what fits the device's shared memory per CTA (about 56K weights on this
+ * part), larger values give MEGO_EINVAL.  Keeps the launch shape and the
+ * per-filter B, status and q of a previous bound.  A filter whose staging
+ * copy does not land within the bounded wait is skipped and gets status
+ * MEGO_ETIMEOUT.  Any threshold gives the same results. */
+mego_status mego_batch_set_smem(mego_batch* b, int32_t smem_max_n, void* stream);
+/* Time every launch shape (threads x particles per thread) and every
+ * shared-memory threshold in {0, 4096, 16384, 49152} (those the device
+ * allows) on the batch as planned (outputs are overwritten), and keep the
+ * fastest pair.  The loop over iterations is not a knob: one generator call
+ * serves five iterations (the Megopolis uniforms), so the chain always
+ * advances five iterations per step. */
 mego_status mego_batch_autotune(mego_batch* b, int32_t reps, float* best_ms,
                                 void* stream);
 mego_status mego_batch_graph(mego_batch* b, double eps, int32_t b_max,

@@ -73,7 +73,9 @@ class BatchHandle(ctypes.Structure):
                 ("total_chunks", ctypes.c_uint64), ("d_B", ctypes.c_void_p),
                 ("d_status", ctypes.c_void_p), ("d_q", ctypes.c_void_p),
                 ("cfg", LaunchCfg), ("grid", ctypes.c_int32), ("graph_exec", ctypes.c_void_p),
-                ("graph_kernels", ctypes.c_int32)]
+                ("graph_kernels", ctypes.c_int32), ("smem_max_n", ctypes.c_int32),
+                ("smem_filters", ctypes.c_int32), ("smem_bytes", ctypes.c_size_t),
+                ("h_filters", ctypes.c_void_p)]
 
 
 class Request(ctypes.Structure):
@@ -141,6 +143,7 @@ def _load():
         "mego_batch_bound": ([ctypes.POINTER(BatchHandle), f64, i32, vp], ci),
         "mego_batch_resample": ([ctypes.POINTER(BatchHandle), vp], ci),
         "mego_batch_set_shape": ([ctypes.POINTER(BatchHandle), i32, i32], ci),
+        "mego_batch_set_smem": ([ctypes.POINTER(BatchHandle), i32, vp], ci),
         "mego_batch_autotune": ([ctypes.POINTER(BatchHandle), i32,
                                  ctypes.POINTER(ctypes.c_float), vp], ci),
         "mego_batch_graph": ([ctypes.POINTER(BatchHandle), f64, i32, vp], ci),
@@ -542,6 +545,12 @@ class Batch:
         _check(_load().mego_batch_set_shape(ctypes.byref(self.handle), int(threads), int(ppt)),
                "mego_batch_set_shape")
 
+    def set_smem(self, smem_max_n: int, stream=None):
+        """Filters of at most smem_max_n weights: one CTA each, from shared
+        memory (0: none)."""
+        _check(_load().mego_batch_set_smem(ctypes.byref(self.handle), int(smem_max_n),
+                                           _stream(stream)), "mego_batch_set_smem")
+
     def autotune(self, reps: int = 3, stream=None) -> float:
         ms = ctypes.c_float()
         _check(_load().mego_batch_autotune(ctypes.byref(self.handle), int(reps),
@@ -552,7 +561,8 @@ class Batch:
     @property
     def shape(self):
         return {"threads": self.handle.cfg.threads, "ppt": self.handle.cfg.ppt,
-                "grid": self.handle.grid}
+                "grid": self.handle.grid, "smem_max_n": self.handle.smem_max_n,
+                "smem_filters": self.handle.smem_filters}
 
     def capture(self, eps: float = 0.01, b_max: int = B_MAX, stream=None):
         """Capture [bound if eps > 0] + resample into a CUDA graph (needs a

@@ -15,6 +15,7 @@
 // ancestors are the same alone (mego_resample_gather with that seed and
 // stream id) and in any batch.
 #include <algorithm>
+#include <cstddef>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -77,11 +78,18 @@ struct PlanHeader {
   // (its chains set the length of the launch): (bits of float((B + 1) x
   // items) << 32) | ~f, the largest wins (ties: the lowest f); 0 = none.
   unsigned long long heavy;
+  // Shared-memory phase: filters of at most smem_max_n weights are resampled
+  // whole by one CTA each (their weights staged in shared memory), claimed
+  // through smem_next before the warp-level queue; they own no work items.
+  uint32_t smem_next;
+  uint32_t smem_count;
+  uint32_t smem_max_n;
+  uint32_t reserved;
 };
-static_assert(sizeof(PlanHeader) == 32, "plan header layout");
+static_assert(sizeof(PlanHeader) == 48, "plan header layout");
 
 struct PlanLayout {
-  size_t filters, item_prefix, chunk_prefix, B, status, q, parts, total;
+  size_t filters, item_prefix, chunk_prefix, B, status, q, smem_list, parts, total;
 };
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -108,6 +116,9 @@ PlanLayout layout_for(uint32_t count, uint64_t total_chunks) {
   L.q = off;
   off += sizeof(double) * count;
   off = align_up(off, 16);
+  L.smem_list = off;  // filter indices of the shared-memory phase, largest first
+  off += sizeof(uint32_t) * count;
+  off = align_up(off, 16);
   L.parts = off;
   off += sizeof(Partial) * total_chunks;
   L.total = align_up(off, 256);
@@ -116,7 +127,8 @@ PlanLayout layout_for(uint32_t count, uint64_t total_chunks) {
 
 struct BatchArgs {
   unsigned char* plan;
-  size_t off_filters, off_item_prefix, off_chunk_prefix, off_B, off_status, off_q, off_parts;
+  size_t off_filters, off_item_prefix, off_chunk_prefix, off_B, off_status, off_q, off_smem_list,
+      off_parts;
   RoundKeys K;
 };
 
@@ -347,7 +359,48 @@ __global__ void __launch_bounds__(256) batch_finalize_kernel(const __grid_consta
 // ---------------------------------------------------------------------------
 // Persistent resample over the work queue.
 
-template <int VARIANT, int P, int GATHER>
+// Stage w[0, n) of one filter into dynamic shared memory for a CTA that
+// stages filter after filter: the 16-byte aligned whole part by bulk async
+// copies on the CTA's barrier `bar` (phase parity `phase`, flipped by each
+// bulk staging), the rest by plain loads.  Returns 0 when staged; 1 when the
+// bounded wait expired but a second bounded wait saw the copy land (the
+// filter is skipped); 2 when the copy did not land either (the CTA must stop
+// using its shared memory).  Uniform across the CTA.
+__device__ __forceinline__ int stage_filter(const float* w, uint32_t n, uint64_t* bar,
+                                            uint32_t& phase) {
+  float* s_w = reinterpret_cast<float*>(g_dyn_smem);
+  const uint32_t n4 = n & ~3u;
+  const bool bulk = ((reinterpret_cast<uintptr_t>(w) & 15u) == 0u) && n4 > 0u;
+  if (bulk && threadIdx.x == 0) {
+    const uint32_t bytes = n4 * 4u;
+    mbar_expect_tx(bar, bytes);
+    for (uint32_t off = 0; off < bytes; off += kStageChunk) {
+      const uint32_t len = (bytes - off) < kStageChunk ? (bytes - off) : kStageChunk;
+      bulk_g2s(reinterpret_cast<char*>(s_w) + off, reinterpret_cast<const char*>(w) + off, len,
+               bar);
+    }
+  }
+  for (uint32_t t = (bulk ? n4 : 0u) + threadIdx.x; t < n; t += blockDim.x) s_w[t] = __ldg(w + t);
+  int status = 0;
+  if (bulk) {
+    const bool done = mbar_wait_bounded(bar, phase, kMaxPolls);
+    if (!__syncthreads_and(done ? 1 : 0)) {
+      int lost = 0;
+      if (threadIdx.x == 0) lost = mbar_wait_bounded(bar, phase, kMaxPolls) ? 0 : 1;
+      status = __syncthreads_or(lost) ? 2 : 1;
+    }
+    phase ^= 1u;
+  }
+  __syncthreads();
+  return status;
+}
+
+// WITH_SMEM: first the shared-memory phase -- each CTA claims whole small
+// filters (the plan's smem list), stages a filter's weights once and splits
+// its 32-particle segments among its warps (run on the shared-memory path) --
+// then the warp-level queue over the other filters' work items.  Without it
+// the kernel is the warp-level queue alone.
+template <int VARIANT, int P, int GATHER, bool WITH_SMEM>
 __global__ void __launch_bounds__(max_threads_for(P))
 batch_resample_kernel(const __grid_constant__ BatchArgs a) {
   __shared__ int2 s_win[kMaxWarps][32];
@@ -362,7 +415,62 @@ batch_resample_kernel(const __grid_constant__ BatchArgs a) {
   const unsigned long long heavy = h->heavy;
   const uint32_t item_segs = h->item_segs;
   int2* win = s_win[threadIdx.x >> 5];
+  bool healthy = true;
+  if constexpr (WITH_SMEM) {
+    const uint32_t* sl = reinterpret_cast<const uint32_t*>(a.plan + a.off_smem_list);
+    int32_t* St = reinterpret_cast<int32_t*>(a.plan + a.off_status);
+    const uint32_t nsm = h->smem_count;
+    __shared__ uint32_t s_claim;
+    __shared__ __align__(8) uint64_t s_bar;
+    if (threadIdx.x == 0) mbar_init(&s_bar, 1u);
+    __syncthreads();
+    uint32_t phase = 0u;
+    const uint32_t wpb = blockDim.x >> 5, wi = threadIdx.x >> 5;
+    for (;;) {
+      if (threadIdx.x == 0) s_claim = atomicAdd(&h->smem_next, 1u);
+      __syncthreads();
+      const uint32_t e = s_claim;
+      __syncthreads();  // every thread has read the claim before the next one
+      if (e >= nsm) break;
+      const uint32_t f = __ldg(sl + e);
+      const FilterDev d = F[f];
+      const int B = d.B >= 0 ? d.B : Bb[f];
+      if (B < 0) continue;  // the bound failed for this filter: write nothing
+      const int st = stage_filter(d.w, d.n, &s_bar, phase);
+      if (st != 0) {
+        if (threadIdx.x == 0) St[f] = MEGO_ETIMEOUT;
+        if (st == 2) {
+          healthy = false;
+          break;
+        }
+        continue;
+      }
+      Problem p;
+      p.w = d.w;
+      p.anc = d.anc;
+      p.x_in = d.x_in;
+      p.x_out = d.x_out;
+      p.fault = nullptr;
+      p.ld = d.ld;
+      p.n = d.n;
+      p.nseg = (d.n + 31u) / 32u;
+      p.dim = d.dim;
+      p.nw = 1u;
+      p.npart = d.n;
+      p.stage_polls = kMaxPolls;
+      p.S = stream_key(a.K, d.sid);
+      // The warps of the CTA split the filter's batches of P segments.
+      const uint64_t nbat = (p.nseg + P - 1u) / P;
+      const uint32_t seg_lo = static_cast<uint32_t>(nbat * wi / wpb) * P;
+      const uint32_t seg_hi =
+          min(p.nseg, static_cast<uint32_t>(nbat * (wi + 1u) / wpb) * static_cast<uint32_t>(P));
+      OffsetWindow ow{0u, false};
+      run_segments<VARIANT, P, true, GATHER, false>(p, a.K, B, seg_lo, seg_hi, lane, win, ow);
+      __syncthreads();  // all warps are done with the weights before the next staging
+    }
+  }
   for (;;) {
+    if (!healthy) break;
     uint32_t item = 0;
     if (lane == 0) item = atomicAdd(&h->next, 1u);
     item = __shfl_sync(0xFFFFFFFFu, item, 0);
@@ -394,85 +502,100 @@ batch_resample_kernel(const __grid_constant__ BatchArgs a) {
     OffsetWindow ow{0u, false};
     run_segments<VARIANT, P, false, GATHER, false>(p, a.K, B, seg_lo, seg_hi, lane, win, ow);
   }
-  // The last warp out resets the queue for the next launch of this plan.
+  // The last warp out resets the queues for the next launch of this plan.
   if (lane == 0) {
     __threadfence();
     const uint32_t warps = gridDim.x * (blockDim.x >> 5);
     if (atomicAdd(&h->done, 1u) == warps - 1u) {
       h->next = 0u;
+      h->smem_next = 0u;
       h->done = 0u;
       __threadfence();
     }
   }
 }
 
-template <int V, int P, int G>
-cudaError_t launch_batch_one(int grid, int threads, const BatchArgs& a, cudaStream_t st) {
-  return launch_after(batch_resample_kernel<V, P, G>, dim3(grid), dim3(threads), 0, st, a);
+template <int V, int P, int G, bool S>
+cudaError_t launch_batch_one(int grid, int threads, size_t smem, const BatchArgs& a,
+                             cudaStream_t st) {
+  auto* k = &batch_resample_kernel<V, P, G, S>;
+  if (S) {
+    const cudaError_t e = enable_large_smem(reinterpret_cast<const void*>(k));
+    if (e != cudaSuccess) return e;
+  }
+  return launch_after(k, dim3(grid), dim3(threads), smem, st, a);
 }
 
-template <int V, int P, int G>
+template <int V, int P, int G, bool S>
 const void* batch_ptr_one() {
-  return reinterpret_cast<const void*>(&batch_resample_kernel<V, P, G>);
+  return reinterpret_cast<const void*>(&batch_resample_kernel<V, P, G, S>);
 }
 
-template <int V, int G>
-cudaError_t launch_batch_p(int ppt, int grid, int threads, const BatchArgs& a, cudaStream_t st) {
+template <int V, int G, bool S>
+cudaError_t launch_batch_p(int ppt, int grid, int threads, size_t smem, const BatchArgs& a,
+                           cudaStream_t st) {
   switch (ppt) {
-    case 1: return launch_batch_one<V, 1, G>(grid, threads, a, st);
-    case 2: return launch_batch_one<V, 2, G>(grid, threads, a, st);
-    case 4: return launch_batch_one<V, 4, G>(grid, threads, a, st);
+    case 1: return launch_batch_one<V, 1, G, S>(grid, threads, smem, a, st);
+    case 2: return launch_batch_one<V, 2, G, S>(grid, threads, smem, a, st);
+    case 4: return launch_batch_one<V, 4, G, S>(grid, threads, smem, a, st);
     case 6:
-      if constexpr (V == kMegopolis) return launch_batch_one<V, 6, G>(grid, threads, a, st);
+      if constexpr (V == kMegopolis) return launch_batch_one<V, 6, G, S>(grid, threads, smem, a, st);
       return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
 }
 
-template <int V, int G>
+template <int V, int G, bool S>
 const void* batch_ptr_p(int ppt) {
   switch (ppt) {
-    case 1: return batch_ptr_one<V, 1, G>();
-    case 2: return batch_ptr_one<V, 2, G>();
-    case 4: return batch_ptr_one<V, 4, G>();
+    case 1: return batch_ptr_one<V, 1, G, S>();
+    case 2: return batch_ptr_one<V, 2, G, S>();
+    case 4: return batch_ptr_one<V, 4, G, S>();
     case 6:
-      if constexpr (V == kMegopolis) return batch_ptr_one<V, 6, G>();
+      if constexpr (V == kMegopolis) return batch_ptr_one<V, 6, G, S>();
       return nullptr;
     default: return nullptr;
   }
 }
 
-template <int V>
-cudaError_t launch_batch_v(int gather, int ppt, int grid, int threads, const BatchArgs& a,
-                           cudaStream_t st) {
+template <int V, bool S>
+cudaError_t launch_batch_v(int gather, int ppt, int grid, int threads, size_t smem,
+                           const BatchArgs& a, cudaStream_t st) {
   switch (gather) {
-    case kGatherNone: return launch_batch_p<V, kGatherNone>(ppt, grid, threads, a, st);
-    case kGatherSoa: return launch_batch_p<V, kGatherSoa>(ppt, grid, threads, a, st);
-    case kGatherAos4: return launch_batch_p<V, kGatherAos4>(ppt, grid, threads, a, st);
+    case kGatherNone: return launch_batch_p<V, kGatherNone, S>(ppt, grid, threads, smem, a, st);
+    case kGatherSoa: return launch_batch_p<V, kGatherSoa, S>(ppt, grid, threads, smem, a, st);
+    case kGatherAos4: return launch_batch_p<V, kGatherAos4, S>(ppt, grid, threads, smem, a, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
-template <int V>
+template <int V, bool S>
 const void* batch_ptr_v(int gather, int ppt) {
   switch (gather) {
-    case kGatherNone: return batch_ptr_p<V, kGatherNone>(ppt);
-    case kGatherSoa: return batch_ptr_p<V, kGatherSoa>(ppt);
-    case kGatherAos4: return batch_ptr_p<V, kGatherAos4>(ppt);
+    case kGatherNone: return batch_ptr_p<V, kGatherNone, S>(ppt);
+    case kGatherSoa: return batch_ptr_p<V, kGatherSoa, S>(ppt);
+    case kGatherAos4: return batch_ptr_p<V, kGatherAos4, S>(ppt);
     default: return nullptr;
   }
 }
 
-const void* batch_kernel_ptr(int variant, int gather, int ppt) {
-  return variant == MEGO_MEGOPOLIS ? batch_ptr_v<kMegopolis>(gather, ppt)
-                                   : batch_ptr_v<kMetropolis>(gather, ppt);
+const void* batch_kernel_ptr(int variant, int gather, int ppt, bool smem) {
+  if (smem)
+    return variant == MEGO_MEGOPOLIS ? batch_ptr_v<kMegopolis, true>(gather, ppt)
+                                     : batch_ptr_v<kMetropolis, true>(gather, ppt);
+  return variant == MEGO_MEGOPOLIS ? batch_ptr_v<kMegopolis, false>(gather, ppt)
+                                   : batch_ptr_v<kMetropolis, false>(gather, ppt);
 }
 
-cudaError_t launch_batch(int variant, int gather, int ppt, int grid, int threads,
+cudaError_t launch_batch(int variant, int gather, int ppt, int grid, int threads, size_t smem,
                          const BatchArgs& a, cudaStream_t st) {
+  if (smem > 0)
+    return variant == MEGO_MEGOPOLIS
+               ? launch_batch_v<kMegopolis, true>(gather, ppt, grid, threads, smem, a, st)
+               : launch_batch_v<kMetropolis, true>(gather, ppt, grid, threads, smem, a, st);
   return variant == MEGO_MEGOPOLIS
-             ? launch_batch_v<kMegopolis>(gather, ppt, grid, threads, a, st)
-             : launch_batch_v<kMetropolis>(gather, ppt, grid, threads, a, st);
+             ? launch_batch_v<kMegopolis, false>(gather, ppt, grid, threads, 0, a, st)
+             : launch_batch_v<kMetropolis, false>(gather, ppt, grid, threads, 0, a, st);
 }
 
 int gather_of(int layout, bool has_state) {
@@ -491,20 +614,24 @@ BatchArgs args_of(const mego_batch* b) {
   a.off_B = L.B;
   a.off_status = L.status;
   a.off_q = L.q;
+  a.off_smem_list = L.smem_list;
   a.off_parts = L.parts;
   a.K = make_round_keys(b->seed);
   return a;
 }
 
-// Grid of the persistent kernel: every SM full of resident CTAs.
-mego_status shape_for(int variant, int gather, int threads, int ppt, int* grid) {
-  const void* k = batch_kernel_ptr(variant, gather, ppt);
+// Grid of the persistent kernel: every SM full of resident CTAs (with
+// `smem` bytes of dynamic shared memory each when the plan has a
+// shared-memory phase).
+mego_status shape_for(int variant, int gather, int threads, int ppt, size_t smem, int* grid) {
+  const void* k = batch_kernel_ptr(variant, gather, ppt, smem > 0);
   if (!k) return MEGO_EINVAL;
   int dev = 0, sms = 0, occ = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return MEGO_ECUDA;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return MEGO_ECUDA;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, threads, 0) != cudaSuccess) {
+  if (smem > 0 && enable_large_smem(k) != cudaSuccess) return MEGO_EINVAL;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, threads, smem) != cudaSuccess) {
     cudaGetLastError();
     return MEGO_ECUDA;
   }
@@ -543,19 +670,34 @@ mego_status mego_batch_plan(const mego_filter* h_filters, int32_t count, int var
                             mego_batch* out, void* stream) {
   // Pageable staging: the copy has read it by the time cudaMemcpyAsync returns.
   std::vector<unsigned char> host;
-  return mego::batch_plan_staged(h_filters, count, variant, layout, seed, d_plan, plan_bytes,
-                                 &host, nullptr, 0, out, stream);
+  if (!out) return MEGO_EINVAL;
+  return mego::batch_plan_staged(h_filters, count, variant, layout, seed, 0, d_plan, plan_bytes,
+                                 &host, nullptr, 0, out, stream, false);
 }
 
 }  // extern "C"
 
 namespace mego {
 
+// Largest smem_max_n the device allows: the filter's weights (rounded up to
+// 16 bytes) next to the kernel's static shared memory (the per-warp offset
+// tables, the claim and the barrier: under 4 KiB).
+int32_t smem_limit_n() {
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+      cudaSuccess)
+    return 0;
+  return optin > 4096 ? ((optin - 4096) / 16) * 4 : 0;
+}
+
 mego_status batch_plan_staged(const mego_filter* h_filters, int32_t count, int variant,
-                              int layout, uint64_t seed, void* d_plan, size_t plan_bytes,
-                              std::vector<unsigned char>* pageable, void* staging,
-                              size_t staging_bytes, mego_batch* out, void* stream) {
+                              int layout, uint64_t seed, int32_t smem_max_n, void* d_plan,
+                              size_t plan_bytes, std::vector<unsigned char>* pageable,
+                              void* staging, size_t staging_bytes, mego_batch* out,
+                              void* stream, bool replan) {
   if (!h_filters || count < 1 || !d_plan || !out) return MEGO_EINVAL;
+  if (smem_max_n < 0 || smem_max_n > smem_limit_n()) return MEGO_EINVAL;
   if (variant != MEGO_MEGOPOLIS && variant != MEGO_METROPOLIS) return MEGO_EINVAL;
   if (layout != MEGO_LAYOUT_SOA && layout != MEGO_LAYOUT_AOS4) return MEGO_EINVAL;
   if (reinterpret_cast<uintptr_t>(d_plan) & 255u) return MEGO_EINVAL;
@@ -602,7 +744,9 @@ mego_status batch_plan_staged(const mego_filter* h_filters, int32_t count, int v
   uint32_t* ip = reinterpret_cast<uint32_t*>(host + L.item_prefix);
   uint32_t* cp = reinterpret_cast<uint32_t*>(host + L.chunk_prefix);
   int32_t* Bv = reinterpret_cast<int32_t*>(host + L.B);
+  uint32_t* sl = reinterpret_cast<uint32_t*>(host + L.smem_list);
   uint64_t it = 0, ch = 0;
+  uint32_t nsm = 0, smem_n = 0;
   for (int32_t f = 0; f < count; ++f) {
     const mego_filter& d = h_filters[f];
     F[f] = FilterDev{d.w, d.anc, d.x_in, d.x_out, d.ld, static_cast<uint32_t>(d.n), d.B,
@@ -610,10 +754,21 @@ mego_status batch_plan_staged(const mego_filter* h_filters, int32_t count, int v
     ip[f] = static_cast<uint32_t>(it);
     cp[f] = static_cast<uint32_t>(ch);
     Bv[f] = d.B;
+    ch += (static_cast<uint64_t>(d.n) + kChunk - 1) / kChunk;
+    if (d.n <= smem_max_n) {  // shared-memory phase: a whole filter per CTA, no items
+      sl[nsm++] = static_cast<uint32_t>(f);
+      if (static_cast<uint32_t>(d.n) > smem_n) smem_n = static_cast<uint32_t>(d.n);
+      continue;
+    }
     const uint64_t nseg = (static_cast<uint64_t>(d.n) + 31u) / 32u;
     it += (nseg + item_segs - 1) / item_segs;
-    ch += (static_cast<uint64_t>(d.n) + kChunk - 1) / kChunk;
   }
+  // Largest filters first, so the long stagings start early.
+  std::stable_sort(sl, sl + nsm, [&](uint32_t x, uint32_t y) {
+    return h_filters[x].n > h_filters[y].n;
+  });
+  reinterpret_cast<PlanHeader*>(host)->smem_count = nsm;
+  reinterpret_cast<PlanHeader*>(host)->smem_max_n = static_cast<uint32_t>(smem_max_n);
   reinterpret_cast<PlanHeader*>(host)->total_items = static_cast<uint32_t>(it);
   items = it;
   ip[count] = static_cast<uint32_t>(it);
@@ -628,10 +783,30 @@ mego_status batch_plan_staged(const mego_filter* h_filters, int32_t count, int v
     if (k > heavy) heavy = k;
   }
   reinterpret_cast<PlanHeader*>(host)->heavy = heavy;
-  if (cudaMemcpyAsync(d_plan, host, L.parts, cudaMemcpyHostToDevice,
-                      static_cast<cudaStream_t>(stream)) != cudaSuccess)
-    return MEGO_ECUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!replan) {
+    if (cudaMemcpyAsync(d_plan, host, L.parts, cudaMemcpyHostToDevice, st) != cudaSuccess)
+      return MEGO_ECUDA;
+  } else {
+    // A new shared-memory threshold for a plan in use: keep the heavy filter
+    // the last bound found (a stale one only reorders the queue) and the
+    // per-filter B, status and q, which a bound may already have written.
+    const size_t heavy_off = offsetof(PlanHeader, heavy);
+    const size_t after = heavy_off + sizeof(unsigned long long);
+    if (cudaMemcpyAsync(d_plan, host, heavy_off, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(static_cast<unsigned char*>(d_plan) + after, host + after, L.B - after,
+                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(static_cast<unsigned char*>(d_plan) + L.smem_list, host + L.smem_list,
+                        L.parts - L.smem_list, cudaMemcpyHostToDevice, st) != cudaSuccess)
+      return MEGO_ECUDA;
+  }
+  const mego_launch_cfg keep = out->cfg;
   std::memset(out, 0, sizeof *out);
+  out->h_filters = h_filters;
+  out->smem_max_n = smem_max_n;
+  out->smem_filters = static_cast<int32_t>(nsm);
+  out->smem_bytes = nsm ? (static_cast<size_t>(smem_n) * 4u + 15u) & ~static_cast<size_t>(15u)
+                        : 0u;
   out->d_plan = d_plan;
   out->plan_bytes = L.total;
   out->count = count;
@@ -647,14 +822,19 @@ mego_status batch_plan_staged(const mego_filter* h_filters, int32_t count, int v
   // Default shape: Megopolis takes one whole work item per warp (six chains
   // per thread in 128-thread CTAs, or four in 256-thread CTAs, following the
   // item size); Metropolis is bound by scattered loads and takes two.
-  const int ppt = variant == MEGO_MEGOPOLIS ? static_cast<int>(item_segs) : 2;
-  const int threads = ppt == 6 ? 128 : 256;
+  // A re-plan keeps the caller's shape.
+  int ppt = variant == MEGO_MEGOPOLIS ? static_cast<int>(item_segs) : 2;
+  int threads = ppt == 6 ? 128 : 256;
+  if (replan && keep.threads > 0) {
+    ppt = keep.ppt;
+    threads = keep.threads;
+  }
   out->cfg.threads = threads;
   out->cfg.ppt = ppt;
-  out->cfg.path = MEGO_PATH_GLOBAL;
+  out->cfg.path = nsm ? MEGO_PATH_SMEM : MEGO_PATH_GLOBAL;
   out->cfg.ctas_per_sm = 0;
   int grid = 0;
-  const mego_status s = shape_for(variant, out->gather, threads, ppt, &grid);
+  const mego_status s = shape_for(variant, out->gather, threads, ppt, out->smem_bytes, &grid);
   if (s != MEGO_OK) return s;
   out->grid = grid;
   return MEGO_OK;
@@ -684,7 +864,7 @@ mego_status mego_batch_resample(const mego_batch* b, void* stream) {
   using namespace mego;
   if (!b || !b->d_plan || b->grid < 1) return MEGO_EINVAL;
   const BatchArgs a = args_of(b);
-  if (launch_batch(b->variant, b->gather, b->cfg.ppt, b->grid, b->cfg.threads, a,
+  if (launch_batch(b->variant, b->gather, b->cfg.ppt, b->grid, b->cfg.threads, b->smem_bytes, a,
                    static_cast<cudaStream_t>(stream)) != cudaSuccess)
     return MEGO_ECUDA;
   count_launches(1);
@@ -697,7 +877,7 @@ mego_status mego_batch_set_shape(mego_batch* b, int32_t threads, int32_t ppt) {
       (ppt != 1 && ppt != 2 && ppt != 4 && ppt != 6))
     return MEGO_EINVAL;
   int grid = 0;
-  const mego_status s = shape_for(b->variant, b->gather, threads, ppt, &grid);
+  const mego_status s = shape_for(b->variant, b->gather, threads, ppt, b->smem_bytes, &grid);
   if (s != MEGO_OK) return s;
   b->cfg.threads = threads;
   b->cfg.ppt = ppt;
@@ -705,8 +885,22 @@ mego_status mego_batch_set_shape(mego_batch* b, int32_t threads, int32_t ppt) {
   return MEGO_OK;
 }
 
+mego_status mego_batch_set_smem(mego_batch* b, int32_t smem_max_n, void* stream) {
+  if (!b || !b->d_plan || !b->h_filters || b->count < 1) return MEGO_EINVAL;
+  if (b->graph_exec) return MEGO_EINVAL;  // a captured graph holds the old launch
+  std::vector<unsigned char> host;
+  mego_batch nb = *b;
+  const mego_status s = mego::batch_plan_staged(
+      b->h_filters, b->count, b->variant, b->layout, b->seed, smem_max_n, b->d_plan,
+      b->plan_bytes, &host, nullptr, 0, &nb, stream, true);
+  if (s != MEGO_OK) return s;
+  *b = nb;
+  return MEGO_OK;
+}
+
 mego_status mego_batch_autotune(mego_batch* b, int32_t reps, float* best_ms, void* stream) {
   if (!b || reps < 1 || reps > 100) return MEGO_EINVAL;
+  if (b->graph_exec) return MEGO_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return MEGO_ECUDA;
@@ -716,41 +910,59 @@ mego_status mego_batch_autotune(mego_batch* b, int32_t reps, float* best_ms, voi
   }
   const int threads_c[] = {64, 128, 256};
   const int ppt_c[] = {1, 2, 4, 6};
+  // Shared-memory thresholds: none, then filters of up to 16, 64 and 192 KiB
+  // of weights (only with the caller's filters at hand, to re-plan).
+  const int32_t smem_c[] = {0, 4096, 16384, 49152};
+  const int32_t smem_cap = mego::smem_limit_n();
   int best_t = b->cfg.threads, best_p = b->cfg.ppt;
+  int32_t best_sm = b->smem_max_n;
   float best = 1e30f;
   mego_status status = MEGO_OK;
-  for (int t : threads_c) {
-    for (int p : ppt_c) {
-      mego_status s = mego_batch_set_shape(b, t, p);
-      if (s == MEGO_EINVAL) continue;
-      if (s == MEGO_OK) s = mego_batch_resample(b, stream);  // warm-up
-      float total = 0.0f;
-      for (int r = 0; r < reps && s == MEGO_OK; ++r) {
-        float ms = 0.0f;
-        if (cudaEventRecord(e0, st) != cudaSuccess) s = MEGO_ECUDA;
-        if (s == MEGO_OK) s = mego_batch_resample(b, stream);
-        if (s == MEGO_OK && (cudaEventRecord(e1, st) != cudaSuccess ||
-                             cudaEventSynchronize(e1) != cudaSuccess ||
-                             cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
-          s = MEGO_ECUDA;
-        total += ms;
+  for (int32_t sm : smem_c) {
+    if (sm > 0 && (!b->h_filters || sm > smem_cap)) continue;
+    if (b->h_filters) {
+      status = mego_batch_set_smem(b, sm, stream);
+      if (status != MEGO_OK) break;
+    } else if (sm != b->smem_max_n) {
+      continue;
+    }
+    for (int t : threads_c) {
+      for (int p : ppt_c) {
+        mego_status s = mego_batch_set_shape(b, t, p);
+        if (s == MEGO_EINVAL) continue;
+        if (s == MEGO_OK) s = mego_batch_resample(b, stream);  // warm-up
+        float total = 0.0f;
+        for (int r = 0; r < reps && s == MEGO_OK; ++r) {
+          float ms = 0.0f;
+          if (cudaEventRecord(e0, st) != cudaSuccess) s = MEGO_ECUDA;
+          if (s == MEGO_OK) s = mego_batch_resample(b, stream);
+          if (s == MEGO_OK && (cudaEventRecord(e1, st) != cudaSuccess ||
+                               cudaEventSynchronize(e1) != cudaSuccess ||
+                               cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+            s = MEGO_ECUDA;
+          total += ms;
+        }
+        if (s != MEGO_OK) {
+          status = s;
+          break;
+        }
+        if (total / reps < best) {
+          best = total / reps;
+          best_t = t;
+          best_p = p;
+          best_sm = sm;
+        }
       }
-      if (s != MEGO_OK) {
-        status = s;
-        break;
-      }
-      if (total / reps < best) {
-        best = total / reps;
-        best_t = t;
-        best_p = p;
-      }
+      if (status != MEGO_OK) break;
     }
     if (status != MEGO_OK) break;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (status != MEGO_OK) return status;
-  const mego_status s = mego_batch_set_shape(b, best_t, best_p);
+  mego_status s = MEGO_OK;
+  if (b->h_filters && best_sm != b->smem_max_n) s = mego_batch_set_smem(b, best_sm, stream);
+  if (s == MEGO_OK) s = mego_batch_set_shape(b, best_t, best_p);
   if (s == MEGO_OK && best_ms) *best_ms = best;
   return s;
 }

@@ -211,9 +211,9 @@ bool mego_server::launch_batch(const std::vector<Req>& reqs, int si, InFlight* f
   if (f->plan_bytes == 0 || f->plan_bytes > plan_slice) return false;
   f->plan_off = static_cast<size_t>(si) * plan_slice;  // this stream's plan slice
   bool ok = mego::batch_plan_staged(filters.data(), static_cast<int32_t>(filters.size()),
-                                    cfg.variant, MEGO_LAYOUT_AOS4, cfg.seed, base + f->plan_off,
-                                    f->plan_bytes, nullptr, staging[si], plan_slice, &f->batch,
-                                    st) == MEGO_OK;
+                                    cfg.variant, MEGO_LAYOUT_AOS4, cfg.seed, 0,
+                                    base + f->plan_off, f->plan_bytes, nullptr, staging[si],
+                                    plan_slice, &f->batch, st, false) == MEGO_OK;
   if (ok && cfg.threads > 0)
     ok = mego_batch_set_shape(&f->batch, cfg.threads,
                               cfg.ppt > 0 ? cfg.ppt : f->batch.cfg.ppt) == MEGO_OK;

@@ -44,7 +44,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_host_only_calls(lib):
     lib.mego_abi_version.restype = ctypes.c_int
-    assert lib.mego_abi_version() == 3
+    assert lib.mego_abi_version() == 4
     lib.mego_status_string.restype = ctypes.c_char_p
     lib.mego_status_string.argtypes = [ctypes.c_int]
     assert lib.mego_status_string(5).decode().startswith("invalid weights")

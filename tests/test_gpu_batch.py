@@ -229,3 +229,79 @@ def test_heaviest_filter_first_keeps_every_result(heavy_at):
                                               mego.MEGOPOLIS,
                                               anc=torch.empty_like(d["anc"]))[0]
             assert torch.equal(alone, d["anc"]), (heavy_at, with_bound, f)
+
+
+@pytest.mark.parametrize("variant", [mego.MEGOPOLIS, mego.METROPOLIS])
+def test_shared_memory_phase_matches_the_oracle(variant):
+    """Filters at or below the shared-memory threshold are resampled whole
+    by one CTA each from shared memory (their weights staged by bulk copy,
+    the ragged tail by plain loads), the rest by the warp-level queue.  Every
+    threshold, the autotuned one and a graph replay give the oracle's
+    ancestors, with fixed and bound-computed B."""
+    sizes = [1, 3, 31, 33, 100, 1001, 4095, 4096, 4097, 5003, 16384, 20001, 49152, 70001]
+    ws = [synthetic.gaussian_weights(n, (k % 5) * 0.9, 4000 + k) for k, n in enumerate(sizes)]
+    filters = [{"w": torch.from_numpy(w_h).to(DEV),
+                "anc": torch.full((w_h.size,), -1, dtype=torch.int32, device=DEV),
+                "B": (7 + k) if k % 4 == 1 else -1, "stream_id": 90 + k}
+               for k, w_h in enumerate(ws)]
+    batch = mego.Batch(filters, variant=variant, seed=SEED)
+    batch.bound(0.01)
+    batch.resample()
+    torch.cuda.synchronize()
+    Bs = batch.B.cpu().numpy()
+    refs = []
+    for k, (d, w_h) in enumerate(zip(filters, ws)):
+        B = d["B"] if d["B"] >= 0 else int(Bs[k])
+        ref = oracle.resample(w_h, B, SEED, variant, stream_id=d["stream_id"])
+        assert np.array_equal(d["anc"].cpu().numpy(), ref), ("global", k)
+        refs.append(ref)
+
+    def check(tag):
+        for k, d in enumerate(filters):
+            assert np.array_equal(d["anc"].cpu().numpy(), refs[k]), (tag, sizes[k])
+
+    for thr in (4096, 16384, 49152):
+        batch.set_smem(thr)
+        assert batch.shape["smem_filters"] == sum(n <= thr for n in sizes)
+        for d in filters:
+            d["anc"].fill_(-1)
+        batch.resample()
+        torch.cuda.synchronize()
+        check(thr)
+    assert (batch.B.cpu().numpy() == Bs).all()          # a re-plan keeps the bound's B
+    batch.set_smem(0)
+    batch.set_smem(16384)
+    batch.autotune(reps=1)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        batch.capture(0.01, stream=side)
+        for _ in range(2):
+            for d in filters:
+                d["anc"].fill_(-1)
+            batch.replay(stream=side)
+        side.synchronize()
+    check("autotuned %s" % batch.shape)
+    with pytest.raises(mego.MegoError):                # a captured graph pins the plan
+        batch.set_smem(4096)
+    batch.close()
+    with pytest.raises(mego.MegoError):                # beyond the shared memory per CTA
+        mego.Batch(filters, variant=variant, seed=SEED).set_smem(1 << 20)
+
+
+def test_shared_memory_phase_with_aos4_gather():
+    sizes = [777, 4096, 9001, 30000]
+    ws = [synthetic.gaussian_weights(n, 2.0, 50 + k) for k, n in enumerate(sizes)]
+    filters = []
+    for k, w_h in enumerate(ws):
+        x = torch.from_numpy(np.ascontiguousarray(synthetic.gaussian_state(w_h.size, 4, k).T)).to(DEV)
+        filters.append({"w": torch.from_numpy(w_h).to(DEV), "x_in": x,
+                        "x_out": torch.empty_like(x), "B": 25 + k, "stream_id": 3 * k})
+    batch = mego.Batch(filters, layout=mego.LAYOUT_AOS4, seed=SEED)
+    batch.set_smem(16384)
+    assert batch.shape["smem_filters"] == 3
+    batch.resample()
+    torch.cuda.synchronize()
+    for k, d in enumerate(filters):
+        ref = oracle.resample(ws[k], d["B"], SEED, mego.MEGOPOLIS, stream_id=d["stream_id"])
+        assert np.array_equal(d["x_out"].cpu().numpy(),
+                              oracle.gather_aos4(d["x_in"].cpu().numpy(), ref)), sizes[k]
