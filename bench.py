@@ -479,6 +479,38 @@ def _sweep_leg(args, mego, synthetic, torch, dev):
     return out
 
 
+def _path_leg(args, mego, synthetic, torch, dev):
+    """Weight path A/B at N = 2^20 (six chains per thread, 128-thread CTAs,
+    B from the bound): per-lane coalesced loads from L2 (the default) against
+    the TMA window path (each warp's windows fetched by 1-D tensor copies
+    into shared memory); median of event-timed launches, L2 flushed."""
+    import statistics as stats
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    anc = torch.empty(N, dtype=torch.int32, device=dev)
+    out = {}
+    for y in (2, 4):
+        w = torch.from_numpy(synthetic.gaussian_weights(N, y, SEED + y)).to(dev)
+        B = int(mego.mego_compute_B(w, EPS, stream=stream)[0].item())
+        cell = {"B": B}
+        for path, name in ((mego.PATH_GLOBAL, "global_ms"), (mego.PATH_TMA, "tma_window_ms")):
+            cfg = {"ppt": 6, "threads": 128, "path": path}
+            ts = []
+            for _ in range(max(5, args.sweep_reps)):
+                flush.zero_()
+                _hold(torch, 1)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                mego.mego_resample_gather(w, B, None, SEED, 0, mego.MEGOPOLIS, anc=anc, cfg=cfg,
+                                          stream=stream)
+                b.record(stream)
+                torch.cuda.synchronize(dev)
+                ts.append(a.elapsed_time(b))
+            cell[name] = stats.median(ts)
+        out[str(y)] = cell
+    return out
+
+
 def _partition_leg(args, mego, synthetic, torch, dev):
     """The partition-size trade-off (Section 5's C1/C2 comparison): at
     N = 2^22, y = 4, B from Eq. 3, the resample time (median of event-timed
@@ -797,6 +829,7 @@ def run_gpu(args):
     serving = _serving_leg(args, mego, synthetic, torch, dev) if args.serve_requests > 0 else None
     sir = _sir_leg(args, mego, synthetic, torch, dev) if args.sir_trajectories > 0 else None
     sweep = _sweep_leg(args, mego, synthetic, torch, dev) if args.sweep_reps > 0 else None
+    paths = _path_leg(args, mego, synthetic, torch, dev) if args.sweep_reps > 0 else None
     partition = (_partition_leg(args, mego, synthetic, torch, dev)
                  if args.partition_runs > 0 and args.sweep_reps > 0 else None)
 
@@ -893,6 +926,7 @@ def run_gpu(args):
         "serving": serving,
         "sir_filter": sir,
         "scaling_sweep_resample_ms": sweep,
+        "weight_path_ab_n2p20": paths,
         "partition_tradeoff": partition,
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT,
@@ -914,6 +948,7 @@ PROFILE_CASES = {
     "mego_global_n2p20_y4": ("megopolis", 20, 4, "global", None),
     "mego_global_n2p20_y0": ("megopolis", 20, 0, "global", None),
     "mego_global_n2p20_y2": ("megopolis", 20, 2, "global", None),
+    "mego_tma_n2p20_y4": ("megopolis", 20, 4, "tma", None),
     "metro_global_n2p20_y4": ("metropolis", 20, 4, "global", None),
     "mego_smem_n2p14_y4": ("megopolis", 14, 4, "smem", None),
     "mego_global_n2p24_y4": ("megopolis", 24, 4, "global", None),
@@ -980,7 +1015,9 @@ def run_case(name: str):
             mego.mego_compute_B(w, EPS, B_dev=B_dev, status=status)
         else:
             variant = mego.MEGOPOLIS if kind == "megopolis" else mego.METROPOLIS
-            cfg = {"path": mego.PATH_SMEM if path == "smem" else mego.PATH_GLOBAL}
+            cfg = {"path": {"smem": mego.PATH_SMEM, "tma": mego.PATH_TMA}.get(path, mego.PATH_GLOBAL)}
+            if path == "tma":
+                cfg.update({"ppt": 6, "threads": 128})
             mego.mego_resample_gather(w, B, None, SEED, 0, variant, x_in=x, x_out=x_out,
                                       layout=layout, anc=anc, cfg=cfg)
     torch.cuda.synchronize()

@@ -74,8 +74,14 @@ typedef enum mego_layout {
 typedef enum mego_path {
   MEGO_PATH_AUTO = 0,
   MEGO_PATH_GLOBAL = 1, /* weights read from L2/HBM with coalesced loads  */
-  MEGO_PATH_SMEM = 2    /* weights staged whole in shared memory by a bulk
+  MEGO_PATH_SMEM = 2,   /* weights staged whole in shared memory by a bulk
                            async copy; needs 4n bytes <= the CTA's limit  */
+  MEGO_PATH_TMA = 3     /* Megopolis only, ppt 4 or 6, n >= 64 ppt, d_w
+                           16-byte aligned: each warp fetches the five
+                           32 ppt-weight windows of a group of iterations
+                           by 1-D TMA tensor copies into shared memory
+                           (measured slower than MEGO_PATH_GLOBAL on GB300:
+                           the chains are bound by arithmetic, not reads) */
 } mego_path;
 
 /* Launch shape.  Any field 0 selects the library's choice.  The result

@@ -42,6 +42,7 @@ LAYOUT_AOS4 = 1
 PATH_AUTO = 0
 PATH_GLOBAL = 1
 PATH_SMEM = 2
+PATH_TMA = 3
 
 N_MAX = 1 << 30
 B_MAX = 1 << 24

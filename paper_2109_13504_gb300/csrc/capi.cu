@@ -13,6 +13,8 @@
 #include <tuple>
 #include <utility>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include "../../include/megopolis.h"
@@ -126,11 +128,17 @@ mego_status choose_shape(int variant, uint32_t n, int gather, const mego_launch_
   int path = (cfg && cfg->path) ? cfg->path : MEGO_PATH_AUTO;
   if (path == MEGO_PATH_AUTO)
     path = (w_bytes <= 96u * 1024u) ? MEGO_PATH_SMEM : MEGO_PATH_GLOBAL;
-  if (path != MEGO_PATH_SMEM && path != MEGO_PATH_GLOBAL) return MEGO_EINVAL;
+  if (path != MEGO_PATH_SMEM && path != MEGO_PATH_GLOBAL && path != MEGO_PATH_TMA)
+    return MEGO_EINVAL;
+  const bool tma = path == MEGO_PATH_TMA;
+  if (tma && (variant != MEGO_MEGOPOLIS || (ppt != 4 && ppt != 6) ||
+              n < 64u * static_cast<uint32_t>(ppt)))
+    return MEGO_EINVAL;
   const bool smem = path == MEGO_PATH_SMEM;
   if (smem && w_bytes + 4096u > static_cast<size_t>(di.smem_optin)) return MEGO_EINVAL;
   const size_t smem_bytes = smem ? w_bytes : 0u;
-  const void* kp = kernel_ptr(variant, ppt, smem, gather);
+  const void* kp = tma ? mego::resample_tma_kernel_ptr(ppt, gather)
+                       : kernel_ptr(variant, ppt, smem, gather);
   if (!kp) return MEGO_EINVAL;
   int occ = occupancy(kp, threads, smem_bytes);
   if (occ < 1) return MEGO_EINVAL;
@@ -146,6 +154,7 @@ mego_status choose_shape(int variant, uint32_t n, int gather, const mego_launch_
   out->smem = smem;
   out->grid = static_cast<int>(grid);
   out->smem_bytes = smem_bytes;
+  out->tma = tma;
   return MEGO_OK;
 }
 
@@ -165,6 +174,37 @@ RoundKeys make_round_keys(uint64_t seed) {
     k1 += kPhiloxW1;
   }
   return K;
+}
+
+// The driver's tensor-map encoder, looked up once through the runtime (so
+// the library does not link the driver library itself).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+bool encode_window_map(CUtensorMap* map, const float* w, uint32_t n, int ppt) {
+  PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+  if (!encode || (reinterpret_cast<uintptr_t>(w) & 15u)) return false;
+  const cuuint64_t gdim[1] = {static_cast<cuuint64_t>(n)};
+  const cuuint64_t gstride[1] = {static_cast<cuuint64_t>(n) * 4u};  // unused for rank 1
+  const cuuint32_t box[1] = {32u * static_cast<cuuint32_t>(ppt)};
+  const cuuint32_t estride[1] = {1u};
+  return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 1, const_cast<float*>(w), gdim, gstride,
+                box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // Constants of the stream word (c2 = stream id) used by the hoisted generator.
@@ -343,8 +383,11 @@ mego_status mego_resample_gather(const float* d_w, int32_t n, int32_t B, const i
   a.p.S = mego::make_stream_key(a.K, stream_id);
   a.B_dev = d_B;
   a.B = d_B ? 0 : B;
+  if (shape.tma && (reinterpret_cast<uintptr_t>(d_w) & 15u)) return MEGO_EINVAL;
+  if (shape.tma && !mego::encode_window_map(&a.tmap, d_w, un, shape.ppt)) return MEGO_ECUDA;
   const cudaError_t e =
-      launch_variant(variant, shape, gather, a, static_cast<cudaStream_t>(stream));
+      shape.tma ? mego::launch_resample_tma(shape, gather, a, static_cast<cudaStream_t>(stream))
+                : launch_variant(variant, shape, gather, a, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return MEGO_ECUDA;
   g_launches.fetch_add(1);
   return MEGO_OK;
@@ -483,7 +526,7 @@ mego_status mego_autotune(const float* d_w, int32_t n, int32_t B, int variant,
   }
   const int threads_c[] = {64, 128, 256};
   const int ppt_c[] = {1, 2, 4, 6, 8};
-  const int path_c[] = {MEGO_PATH_GLOBAL, MEGO_PATH_SMEM};
+  const int path_c[] = {MEGO_PATH_GLOBAL, MEGO_PATH_SMEM, MEGO_PATH_TMA};
   mego_launch_cfg win{0, 0, 0, 0};
   float win_ms = 1e30f;
   mego_status status = MEGO_OK;

@@ -14,6 +14,8 @@
 // partition per warp and iteration for Megopolis.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (the TMA window path's tensor map)
+
 #include "device_common.cuh"
 
 namespace mego {
@@ -44,7 +46,30 @@ struct ResampleArgs {
   const int32_t* B_dev;  // non-null: read B here (device-side bound)
   int32_t B;
   RoundKeys K;           // round keys of the seed
+  CUtensorMap tmap;      // TMA window path: w as a 1-D tensor, box of 32 P weights
 };
+
+// TMA window path state of one warp: a shared-memory ring of the five
+// windows of a group of iterations, the warp's barrier and its phase.
+struct TmaRing {
+  float* ring;             // [kMegoPerCall][32 P] floats
+  uint64_t* bar;
+  const CUtensorMap* map;  // in the kernel's parameter space
+  uint32_t parity;
+  bool ok;                 // false once a window copy missed its bounded wait
+};
+
+// One window: 32 P consecutive weights from w[x] (x a multiple of 32, so
+// the copy starts on a 128-byte boundary) into shared memory, completing
+// on `bar` (1-D tensor copy through the TMA unit).
+__device__ __forceinline__ void tma_window(float* dst, const CUtensorMap* map, uint32_t x,
+                                           uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.1d.shared::cluster.global.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2}], [%3];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(smem_addr(bar))
+      : "memory");
+}
 
 // Per-warp table of the 32 iterations of the current offset window:
 // (wrapped partition base of the warp's first segment, offset o^(b)).
@@ -209,10 +234,16 @@ __device__ __forceinline__ void mego_wrapped_loads(const Problem& a, uint32_t x0
 // offsets.  A chain keeps the column x0 of its last accepted proposal (its
 // index less 32 p, before the reduction modulo n); the ancestor is that
 // column plus 32 p, reduced once after the last iteration.
-template <int P, bool SMEM, int GATHER>
+//
+// TMA (the window path): for a group whose five windows do not run past n,
+// lane 0 fetches the five 32 P-weight windows into the warp's ring by TMA
+// before the generator runs, and the lanes read their rotated columns from
+// shared memory after it; other groups load directly.
+template <int P, bool SMEM, int GATHER, bool TMA = false>
 __device__ __forceinline__ void megopolis_batch(const Problem& a, const RoundKeys& K, int B,
                                                 uint32_t s0, uint32_t seg_hi,
-                                                uint32_t lane, int2* win) {
+                                                uint32_t lane, int2* win,
+                                                TmaRing* tr = nullptr) {
   const uint32_t n = a.n;
   const uint32_t ibase = s0 * 32u + lane;
   float wk[P];
@@ -237,7 +268,10 @@ __device__ __forceinline__ void megopolis_batch(const Problem& a, const RoundKey
       const uint32_t o = mego_offset(K, a.S, static_cast<uint32_t>(b0) + lane, n);
       uint32_t base = s0 * 32u + (o & ~31u);
       base = base >= n ? base - n : base;
-      fast_mask = __ballot_sync(0xFFFFFFFFu, base + 32u * P <= n);
+      // TMA: a tensor copy must also start on a 16-byte boundary (base a
+      // multiple of 4 weights); a base wrapped modulo a ragged n may not be.
+      fast_mask = __ballot_sync(0xFFFFFFFFu,
+                                base + 32u * P <= n && (!TMA || (base & 3u) == 0u));
       __syncwarp();
       win[lane] = make_int2(static_cast<int>(base), static_cast<int>(o));
       __syncwarp();
@@ -251,11 +285,33 @@ __device__ __forceinline__ void megopolis_batch(const Problem& a, const RoundKey
       // A full group of five iterations.
 #pragma unroll
       for (int q = 0; q < U; ++q) x0[q] = mego_column(win[t0 + q], lane);
-      if (((fast_mask >> t0) & kFull) == kFull) {
+      bool fast = ((fast_mask >> t0) & kFull) == kFull;
+      if constexpr (TMA) {
+        // Every window copy in bounds and 16-byte aligned, checked again from
+        // the table itself (the same entries for every lane: uniform).
 #pragma unroll
-        for (int q = 0; q < U; ++q)
+        for (int q = 0; q < U; ++q) {
+          const uint32_t x = static_cast<uint32_t>(win[t0 + q].x);
+          fast = fast && (x & 3u) == 0u && x + 32u * P <= n;
+        }
+      }
+      if (fast) {
+        if constexpr (TMA) {
+          if (lane == 0) {
+            // The ring's previous reads (generic proxy) before these writes.
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(tr->bar, static_cast<uint32_t>(U) * 32u * P * 4u);
 #pragma unroll
-          for (int p = 0; p < P; ++p) wj[q][p] = ldw_at<SMEM>(a.w, x0[q], 32u * p);
+            for (int q = 0; q < U; ++q)
+              tma_window(tr->ring + q * 32 * P, tr->map, static_cast<uint32_t>(win[t0 + q].x),
+                         tr->bar);
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < U; ++q)
+#pragma unroll
+            for (int p = 0; p < P; ++p) wj[q][p] = ldw_at<SMEM>(a.w, x0[q], 32u * p);
+        }
       } else {
 #pragma unroll
         for (int q = 0; q < U; ++q) mego_wrapped_loads<P, SMEM>(a, x0[q], wj[q]);
@@ -263,6 +319,26 @@ __device__ __forceinline__ void megopolis_batch(const Problem& a, const RoundKey
       uint4 r[P];
 #pragma unroll
       for (int p = 0; p < P; ++p) r[p] = ph[p].gen(mh, ml, K);
+      if constexpr (TMA) {
+        if (fast) {
+          if (!mbar_wait_bounded(tr->bar, tr->parity, kMaxPolls)) {
+            // Record the miss, let the copies land before the ring is
+            // abandoned, and write nothing for this batch.
+            tr->ok = false;
+            if (lane == 0) mbar_wait_bounded(tr->bar, tr->parity, kMaxPolls);
+            __syncwarp();
+            return;
+          }
+          tr->parity ^= 1u;
+#pragma unroll
+          for (int q = 0; q < U; ++q) {
+            const uint32_t off = x0[q] - static_cast<uint32_t>(win[t0 + q].x);
+#pragma unroll
+            for (int p = 0; p < P; ++p) wj[q][p] = tr->ring[q * 32 * P + off + 32u * p];
+          }
+          __syncwarp();  // every lane has read the ring before it is refilled
+        }
+      }
 #pragma unroll
       for (int q = 0; q < U; ++q) {
 #pragma unroll
@@ -582,6 +658,40 @@ resample_kernel(const __grid_constant__ ResampleArgs a) {
                                          s_win[threadIdx.x >> 5], ow);
 }
 
+// Megopolis on the TMA window path (global weights): as resample_kernel, with
+// each warp's windows fetched by TMA into a shared-memory ring.  A window
+// copy that misses its bounded wait marks the fault word and the warp stops.
+template <int P, int GATHER>
+__global__ void __launch_bounds__(max_threads_for(P), min_ctas_single(P))
+resample_tma_kernel(const __grid_constant__ ResampleArgs a) {
+  constexpr int W = max_threads_for(P) / 32;
+  __shared__ int2 s_win[kMaxWarps][32];
+  __shared__ __align__(128) float s_ring[W][kMegoPerCall * 32 * P];
+  __shared__ __align__(8) uint64_t s_bar[W];
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t wi = threadIdx.x >> 5;
+  if (lane == 0) mbar_init(&s_bar[wi], 1u);
+  __syncwarp();
+  grid_dependency_wait();  // inputs (weights, a device-side B) written by the predecessor
+  const int B = a.B_dev ? *a.B_dev : a.B;
+  if (B < 0) return;
+  const uint32_t wpb = blockDim.x >> 5;
+  const uint64_t gw = static_cast<uint64_t>(blockIdx.x) * wpb + wi;
+  const uint64_t tw = static_cast<uint64_t>(gridDim.x) * wpb;
+  const uint64_t nbat = (a.p.nseg + P - 1u) / P;
+  const uint32_t seg_lo = static_cast<uint32_t>(nbat * gw / tw) * P;
+  uint32_t seg_hi = static_cast<uint32_t>(nbat * (gw + 1u) / tw) * P;
+  if (seg_hi > a.p.nseg) seg_hi = a.p.nseg;
+  TmaRing tr{s_ring[wi], &s_bar[wi], &a.tmap, 0u, true};
+  for (uint32_t s0 = seg_lo; s0 < seg_hi; s0 += P) {
+    megopolis_batch<P, false, GATHER, true>(a.p, a.K, B, s0, seg_hi, lane, s_win[wi], &tr);
+    if (!tr.ok) {
+      if (lane == 0 && a.p.fault) atomicExch(a.p.fault, kFaultStageTimeout);
+      break;
+    }
+  }
+}
+
 // Host-side launcher for one variant (defined in resample_<variant>.cu).
 struct LaunchShape {
   int threads;
@@ -589,6 +699,7 @@ struct LaunchShape {
   bool smem;
   int grid;
   size_t smem_bytes;
+  bool tma;  // Megopolis TMA window path (ppt 4 or 6)
 };
 
 // Host-side count of kernel launches (capi.cu), reported by mego_launch_count.
@@ -609,6 +720,14 @@ cudaError_t launch_resample(const LaunchShape& s, int gather, const ResampleArgs
 
 template <int VARIANT>
 const void* resample_kernel_ptr(int ppt, bool smem, int gather);
+
+// The TMA window path (Megopolis only; defined in resample_megopolis.cu).
+cudaError_t launch_resample_tma(const LaunchShape& s, int gather, const ResampleArgs& a,
+                                cudaStream_t stream);
+const void* resample_tma_kernel_ptr(int ppt, int gather);
+// Tensor map of w[0, n) as a 1-D float tensor with a box of 32 ppt weights
+// (capi.cu); false if the driver cannot encode it.
+bool encode_window_map(CUtensorMap* map, const float* w, uint32_t n, int ppt);
 
 // Device address of the variant's fault word (for the current device).
 template <int VARIANT>

@@ -414,12 +414,43 @@ def test_autotune_picks_a_shape_and_keeps_results_exact():
     w = _gpu(w_h)
     cfg, ms = mego.mego_autotune(w, 60, mego.MEGOPOLIS)
     assert cfg["threads"] in (64, 128, 256) and cfg["ppt"] in (1, 2, 4, 6, 8)
-    assert cfg["path"] in (mego.PATH_GLOBAL, mego.PATH_SMEM) and ms > 0
+    assert cfg["path"] in (mego.PATH_GLOBAL, mego.PATH_SMEM, mego.PATH_TMA) and ms > 0
     got = _anc(w_h, 60, 5, mego.MEGOPOLIS)            # no cfg: the tuned shape
     assert np.array_equal(got, oracle.resample(w_h, 60, 5, mego.MEGOPOLIS))
     for ppt in (1, 2, 4, 6, 8):
         got = _anc(w_h, 60, 5, mego.MEGOPOLIS, cfg={"ppt": ppt, "threads": 128})
         assert np.array_equal(got, oracle.resample(w_h, 60, 5, mego.MEGOPOLIS))
+
+
+@pytest.mark.parametrize("ppt,threads", [(6, 128), (6, 64), (4, 256), (4, 128)])
+@pytest.mark.parametrize("n", [64 * 6 + 5, 4096 * 3 + 17, 70001, 1 << 20])
+def test_tma_window_path_bit_exact(ppt, threads, n):
+    """The TMA window path (each warp's five windows of a group fetched by
+    1-D tensor copies into shared memory; groups whose windows run past n
+    load directly) gives the oracle's ancestors, with the tail group, B = 0,
+    and ragged n; no window copy misses its wait."""
+    w_h = synthetic.gaussian_weights(n, 3.0, 21)
+    cfg = {"ppt": ppt, "threads": threads, "path": mego.PATH_TMA}
+    for B in (0, 1, 7, 33, 61):
+        got = _anc(w_h, B, 19, mego.MEGOPOLIS, cfg=cfg)
+        assert np.array_equal(got, _oracle_all(w_h, B, 19, mego.MEGOPOLIS)), (n, B)
+    assert mego.mego_device_fault() == 0
+
+
+def test_tma_window_path_arguments():
+    w = torch.ones(4096, dtype=torch.float32, device=DEV)
+    anc = torch.empty(4096, dtype=torch.int32, device=DEV)
+    for variant, ppt in ((mego.METROPOLIS, 6), (mego.MEGOPOLIS, 2)):
+        with pytest.raises(mego.MegoError) as ei:
+            mego.mego_resample_gather(w, 4, None, 1, 0, variant, anc=anc,
+                                      cfg={"ppt": ppt, "path": mego.PATH_TMA})
+        assert ei.value.status == mego.MEGO_EINVAL
+    with pytest.raises(mego.MegoError):          # fewer than 64 x ppt weights
+        mego.mego_resample_gather(w[:300], 4, None, 1, 0, mego.MEGOPOLIS, anc=anc[:300],
+                                  cfg={"ppt": 6, "path": mego.PATH_TMA})
+    with pytest.raises(mego.MegoError):          # a window copy needs 16-byte alignment
+        mego.mego_resample_gather(w[1:], 4, None, 1, 0, mego.MEGOPOLIS, anc=anc[1:],
+                                  cfg={"ppt": 6, "path": mego.PATH_TMA})
 
 
 def test_no_device_faults_after_the_shared_memory_path():
