@@ -11,7 +11,8 @@ exp turns into a relative error of 1.5 a 2^-23; expf adds at most 2 ulp and
 the oracle's final rounding half an ulp; the last term covers subnormals.
 
 Whole vectors are compared up to N = 2^20 (and at 2^22 and 2^24 for one
-weight shape each); the oracle splits the particles over the host's cores
+weight shape each, and at the 2^30 maximum with B = 3); the oracle splits
+the particles over the host's cores
 (its [i0, i1) entry, one contiguous range per task), which gives the same
 array as its single-threaded run.
 """
@@ -182,7 +183,9 @@ def test_whole_vector_above_2p20(log2n, y):
     torch.cuda.empty_cache()
 
 
-def test_maximum_size_sampled():
+def test_maximum_size_whole_vector():
+    """N = MEGO_N_MAX = 2^30 (4 GiB of weights), B = 3, both variants,
+    every particle (the oracle on all host cores takes a few seconds)."""
     n = mego.N_MAX
     try:
         w = torch.empty(n, dtype=torch.float32, device=DEV)
@@ -191,12 +194,12 @@ def test_maximum_size_sampled():
         pytest.skip("not enough device memory for N_MAX")
     w_h = synthetic.uniform_weights(n, 77)
     w.copy_(torch.from_numpy(w_h))
-    rng = np.random.default_rng(0)
-    idx = _sample_idx(n, rng, 300)
     for v in VARIANTS:
+        anc.fill_(-1)
         mego.mego_resample_gather(w, 3, None, 11, 0, v, anc=anc)
-        got = anc[torch.from_numpy(idx).to(DEV)].cpu().numpy()
-        assert np.array_equal(got, oracle.resample_at(w_h, 3, 11, idx, v))
+        got = anc.cpu().numpy()
+        assert np.array_equal(got, _oracle_all(w_h, 3, 11, v)), v
+        del got
     del w, anc
     torch.cuda.empty_cache()
 
