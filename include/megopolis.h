@@ -481,6 +481,12 @@ mego_status mego_probe_read(const void* d_buf, size_t bytes, int32_t reps,
  * count; lets a caller confirm that the CUDA path ran). */
 uint64_t mego_launch_count(void);
 
+/* Size in bytes of the public structs, for bindings that mirror them:
+ * which = 0 mego_launch_cfg, 1 mego_filter, 2 mego_batch, 3 mego_request,
+ * 4 mego_completion, 5 mego_server_cfg, 6 mego_server_stats_t; 0 otherwise.
+ * Host only. */
+size_t mego_struct_size(int32_t which);
+
 #ifdef __cplusplus
 }
 #endif

@@ -317,6 +317,19 @@ const char* mego_status_string(int status) {
 
 uint64_t mego_launch_count(void) { return g_launches.load(); }
 
+size_t mego_struct_size(int32_t which) {
+  switch (which) {
+    case 0: return sizeof(mego_launch_cfg);
+    case 1: return sizeof(mego_filter);
+    case 2: return sizeof(mego_batch);
+    case 3: return sizeof(mego_request);
+    case 4: return sizeof(mego_completion);
+    case 5: return sizeof(mego_server_cfg);
+    case 6: return sizeof(mego_server_stats_t);
+    default: return 0;
+  }
+}
+
 size_t mego_workspace_bytes(int32_t n) {
   (void)n;
   return static_cast<size_t>(mego::kMaxParts) * sizeof(mego::Partial) + 256u;

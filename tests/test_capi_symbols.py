@@ -67,3 +67,16 @@ def test_argument_errors_need_no_gpu(lib):
     assert f(fake, 10, (1 << 24) + 1, 1, 0, 0, out, None) == 1
     assert f(fake, 10, 4, 1, 0, 7, out, None) == 1            # unknown variant
     assert f(fake, 10, 4, 1, 0, 0, ctypes.c_void_p(0x10010), None) == 1  # overlap
+
+
+def test_binding_structs_match_the_header(lib):
+    # The ctypes mirrors in the binding must have the C structs' sizes
+    # (a field added on one side only shifts every later field).
+    mego = pytest.importorskip("paper_2109_13504_gb300")
+    lib.mego_struct_size.restype = ctypes.c_size_t
+    lib.mego_struct_size.argtypes = [ctypes.c_int32]
+    mirrors = [mego.LaunchCfg, mego.Filter, mego.BatchHandle, mego.Request, mego.Completion,
+               mego.ServerCfg, mego.ServerStats]
+    for which, cls in enumerate(mirrors):
+        assert lib.mego_struct_size(which) == ctypes.sizeof(cls), cls.__name__
+    assert lib.mego_struct_size(99) == 0
