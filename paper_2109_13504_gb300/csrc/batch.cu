@@ -19,6 +19,9 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -623,11 +626,26 @@ BatchArgs args_of(const mego_batch* b) {
 // Grid of the persistent kernel: every SM full of resident CTAs (with
 // `smem` bytes of dynamic shared memory each when the plan has a
 // shared-memory phase).
+// The grid per (device, kernel, CTA size, shared memory) is computed once and
+// cached: the serving loop plans a batch for every launch.
 mego_status shape_for(int variant, int gather, int threads, int ppt, size_t smem, int* grid) {
   const void* k = batch_kernel_ptr(variant, gather, ppt, smem > 0);
   if (!k) return MEGO_EINVAL;
-  int dev = 0, sms = 0, occ = 0;
+  int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return MEGO_ECUDA;
+  using Key = std::tuple<int, const void*, int, size_t>;
+  static std::mutex mu;
+  static std::map<Key, int> cache;
+  const Key key(dev, k, threads, smem);
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      *grid = it->second;
+      return MEGO_OK;
+    }
+  }
+  int sms = 0, occ = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return MEGO_ECUDA;
   if (smem > 0 && enable_large_smem(k) != cudaSuccess) return MEGO_EINVAL;
@@ -637,6 +655,8 @@ mego_status shape_for(int variant, int gather, int threads, int ppt, size_t smem
   }
   if (occ < 1) return MEGO_EINVAL;
   *grid = sms * occ;
+  std::lock_guard<std::mutex> lock(mu);
+  cache.emplace(key, *grid);
   return MEGO_OK;
 }
 
@@ -691,13 +711,19 @@ int32_t smem_limit_n() {
   return optin > 4096 ? ((optin - 4096) / 16) * 4 : 0;
 }
 
+// The limit only matters for a shared-memory phase (the serving loop plans
+// every batch without one and skips the device query).
+bool smem_threshold_ok(int32_t smem_max_n) {
+  return smem_max_n == 0 || (smem_max_n > 0 && smem_max_n <= smem_limit_n());
+}
+
 mego_status batch_plan_staged(const mego_filter* h_filters, int32_t count, int variant,
                               int layout, uint64_t seed, int32_t smem_max_n, void* d_plan,
                               size_t plan_bytes, std::vector<unsigned char>* pageable,
                               void* staging, size_t staging_bytes, mego_batch* out,
                               void* stream, bool replan) {
   if (!h_filters || count < 1 || !d_plan || !out) return MEGO_EINVAL;
-  if (smem_max_n < 0 || smem_max_n > smem_limit_n()) return MEGO_EINVAL;
+  if (!smem_threshold_ok(smem_max_n)) return MEGO_EINVAL;
   if (variant != MEGO_MEGOPOLIS && variant != MEGO_METROPOLIS) return MEGO_EINVAL;
   if (layout != MEGO_LAYOUT_SOA && layout != MEGO_LAYOUT_AOS4) return MEGO_EINVAL;
   if (reinterpret_cast<uintptr_t>(d_plan) & 255u) return MEGO_EINVAL;

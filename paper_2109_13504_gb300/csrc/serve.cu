@@ -24,6 +24,10 @@
 
 #include <cuda_runtime.h>
 
+#if defined(__linux__)
+#include <sys/prctl.h>
+#endif
+
 #include "../../include/megopolis.h"
 #include "batch_plan.h"
 
@@ -89,6 +93,12 @@ struct Req {
   mego_request r;
   int64_t t_submit = 0;
   size_t off = 0, bytes = 0;   // arena slot: w | anc | x_in | x_out
+  // Device addresses of the host buffers when they are page-locked (kernels
+  // then read or write them in place), resolved at submission so that the
+  // worker's launch path makes no pointer queries; null: copy instead.
+  const float* w_dev = nullptr;
+  int32_t* anc_dev = nullptr;
+  float* x_out_dev = nullptr;
 };
 
 struct InFlight {
@@ -183,7 +193,7 @@ bool mego_server::launch_batch(const std::vector<Req>& reqs, int si, InFlight* f
     // runs while other batches hold every SM; with host_copies = 2 the bound
     // reads page-locked weights itself (and writes w).  The state the
     // resample gathers from is read at random, so it is always uploaded.
-    const float* w_host = cfg.host_copies == 2 ? host_device_ptr(q.r.h_w) : nullptr;
+    const float* w_host = cfg.host_copies == 2 ? q.w_dev : nullptr;
     if (!w_host &&
         cudaMemcpyAsync(w, q.r.h_w, 4 * un, cudaMemcpyHostToDevice, st) != cudaSuccess)
       return false;
@@ -192,15 +202,13 @@ bool mego_server::launch_batch(const std::vector<Req>& reqs, int si, InFlight* f
         cudaMemcpyAsync(xi, q.r.h_x, 16 * un, cudaMemcpyHostToDevice, st) != cudaSuccess)
       return false;
     if (direct) {
-      if (int32_t* h = host_device_ptr(q.r.h_anc)) {
-        anc = h;
+      if (q.anc_dev) {
+        anc = q.anc_dev;
         anc_direct[k] = 1;
       }
-      if (state) {
-        if (float* h = host_device_ptr(q.r.h_x_out)) {
-          xo = h;
-          xo_direct[k] = 1;
-        }
+      if (state && q.x_out_dev) {
+        xo = q.x_out_dev;
+        xo_direct[k] = 1;
       }
     }
     filters[k] = mego_filter{w, anc, state ? xi : nullptr, state ? xo : nullptr, 4,
@@ -268,6 +276,13 @@ void mego_server::finish(InFlight& f) {
 
 void mego_server::run() {
   cudaSetDevice(device);
+#if defined(__linux__)
+  // The worker polls its in-flight batches every poll_us microseconds while
+  // busy; Linux would otherwise let such a short sleep overrun by its default
+  // 50 us of timer slack, delaying every completion and launch by as much.
+  // (This thread's own setting; it ends with the thread.)
+  prctl(PR_SET_TIMERSLACK, 1000UL, 0UL, 0UL, 0UL);
+#endif
   std::unique_lock<std::mutex> lock(mu);
   while (!stop.load()) {
     // 1. Completions.
@@ -409,6 +424,13 @@ mego_status mego_server_submit(mego_server* s, const mego_request* r) {
   Req q;
   q.r = *r;
   q.t_submit = now_ns();
+  // Page-locked host buffers, resolved here (on the caller's thread) rather
+  // than on the worker's launch path.
+  if (s->cfg.host_copies == 2) q.w_dev = host_device_ptr(r->h_w);
+  if (s->cfg.host_copies != 1) {
+    q.anc_dev = host_device_ptr(r->h_anc);
+    q.x_out_dev = host_device_ptr(r->h_x_out);
+  }
   {
     std::lock_guard<std::mutex> lock(s->mu);
     s->queue.push_back(q);
