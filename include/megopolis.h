@@ -450,6 +450,9 @@ mego_status mego_autotune(const float* d_w, int32_t n, int32_t B, int variant,
  * Device faults of the resample kernels: the shared-memory path waits for
  * its bulk copy of the weights with a bounded number of polls; if the copy
  * has not landed by then, the CTA records a fault (1) and writes nothing.
+ * The TMA window path records 1 the same way.  A library built with
+ * -DMEGO_BOUNDS_CHECK also checks every index the chains form against n and
+ * records an out-of-range one as 2 (using index 0 instead).
  * *h_fault receives the OR of the recorded faults since the last call
  * (0: none), and the record is cleared.  Synchronises the device.
  */

@@ -42,15 +42,24 @@ def _inputs_mtime() -> float:
     return max(os.path.getmtime(f) for f in files)
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _inputs_mtime():
-        return LIB
+# The bounds-checked build (-DMEGO_BOUNDS_CHECK): every index the chains form
+# is checked against n and a bad one is recorded in the fault word instead of
+# being used.  It holds the single-resample entry points only (the C ABI's
+# host code, the bound and the resample kernels) and is built on demand by
+# the test that uses it, not by build().
+CHECKED_SOURCES = ("capi.cu", "bound.cu", "resample_megopolis.cu", "resample_metropolis.cu",
+                   "resample_c1.cu", "resample_c2.cu")
+CHECKED_DIR = os.path.join(BUILD, "checked")
+CHECKED_LIB = os.path.join(CHECKED_DIR, "libmegopolis_checked.so")
+
+
+def _build_lib(srcs, out_dir, lib, defines, verbose, ptxas_info) -> str:
+    os.makedirs(out_dir, exist_ok=True)
     cc = nvcc()
-    extra = ["-Xptxas", "-v"] if ptxas_info else []
+    extra = (["-Xptxas", "-v"] if ptxas_info else []) + ["-D" + d for d in defines]
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src)[:-3] + ".o")
         cmd = [cc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
@@ -61,16 +70,29 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             print(proc.stderr, file=sys.stderr)
         return obj
 
-    srcs = sources()
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 1)) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + ".%d.tmp" % os.getpid()
+    tmp = lib + ".%d.tmp" % os.getpid()
     cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs]
     proc = subprocess.run(cmd, capture_output=True, text=True)
     if proc.returncode != 0:
         raise RuntimeError("nvcc link failed:\n%s" % proc.stderr)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
+
+
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
+    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _inputs_mtime():
+        return LIB
+    return _build_lib(sources(), BUILD, LIB, [], verbose, ptxas_info)
+
+
+def build_checked(force: bool = False, verbose: bool = False) -> str:
+    if (not force and os.path.exists(CHECKED_LIB)
+            and os.path.getmtime(CHECKED_LIB) >= _inputs_mtime()):
+        return CHECKED_LIB
+    srcs = [os.path.join(CSRC, f) for f in CHECKED_SOURCES]
+    return _build_lib(srcs, CHECKED_DIR, CHECKED_LIB, ["MEGO_BOUNDS_CHECK"], verbose, False)
 
 
 if __name__ == "__main__":

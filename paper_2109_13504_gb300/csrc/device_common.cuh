@@ -278,6 +278,8 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 
 // Fault word: set when a bounded wait times out.  Read by mego_sync_status
 // callers through the library's own diagnostics.
-enum : int32_t { kFaultNone = 0, kFaultStageTimeout = 1 };
+// kFaultIndex: a bounds-checked build (-DMEGO_BOUNDS_CHECK) met an index
+// out of range.
+enum : int32_t { kFaultNone = 0, kFaultStageTimeout = 1, kFaultIndex = 2 };
 
 }  // namespace mego

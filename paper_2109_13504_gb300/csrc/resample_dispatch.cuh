@@ -100,10 +100,16 @@ const void* ptr_by_gather(int ppt, int gather) {
 template <>
 cudaError_t launch_resample<MEGO_VARIANT>(const LaunchShape& s, int gather,
                                           const ResampleArgs& a, cudaStream_t st) {
-  if (!s.smem) return by_gather<MEGO_VARIANT, false>(s, gather, a, st);
+#ifdef MEGO_BOUNDS_CHECK
+  const bool report = true;  // index checks report on every path
+#else
+  const bool report = s.smem;
+#endif
+  if (!report) return by_gather<MEGO_VARIANT, false>(s, gather, a, st);
   ResampleArgs b = a;
   b.p.fault = fault_word_address();
-  return by_gather<MEGO_VARIANT, true>(s, gather, b, st);
+  return s.smem ? by_gather<MEGO_VARIANT, true>(s, gather, b, st)
+                : by_gather<MEGO_VARIANT, false>(s, gather, b, st);
 }
 
 template <>

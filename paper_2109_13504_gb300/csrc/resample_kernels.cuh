@@ -71,6 +71,24 @@ __device__ __forceinline__ void tma_window(float* dst, const CUtensorMap* map, u
       : "memory");
 }
 
+// Bounds-checked builds (-DMEGO_BOUNDS_CHECK): every weight or state index a
+// chain forms is checked against n before it is used (for a window of
+// consecutive loads, its last index); a bad one is recorded in the fault
+// word (kFaultIndex) and replaced by 0, so nothing is read out of range.
+// The normal build compiles these checks away.
+__device__ __forceinline__ uint32_t checked(const Problem& a, uint32_t j, uint32_t span = 0u) {
+#ifdef MEGO_BOUNDS_CHECK
+  if (j + span >= a.n || j + span < j) {
+    if (a.fault) atomicOr(a.fault, kFaultIndex);
+    return 0u;
+  }
+#else
+  (void)a;
+  (void)span;
+#endif
+  return j;
+}
+
 // Per-warp table of the 32 iterations of the current offset window:
 // (wrapped partition base of the warp's first segment, offset o^(b)).
 constexpr int kMaxWarps = 8;
@@ -156,8 +174,11 @@ __device__ __forceinline__ bool stage_weights(const Problem& a) {
 // Ancestor output and gather for the P particles of one batch.
 template <int P, int GATHER>
 __device__ __forceinline__ void finish_batch(const Problem& a, uint32_t ibase,
-                                             const uint32_t (&k)[P],
+                                             const uint32_t (&k_in)[P],
                                              const bool (&live)[P]) {
+  uint32_t k[P];
+#pragma unroll
+  for (int p = 0; p < P; ++p) k[p] = live[p] ? checked(a, k_in[p]) : k_in[p];
 #pragma unroll
   for (int p = 0; p < P; ++p)
     if (live[p] && a.anc) (a.anc + ibase)[32u * p] = static_cast<int32_t>(k[p]);
@@ -218,7 +239,7 @@ template <int P, bool SMEM>
 __device__ __forceinline__ void mego_wrapped_loads(const Problem& a, uint32_t x0,
                                                    float (&wj)[P]) {
 #pragma unroll
-  for (int p = 0; p < P; ++p) wj[p] = ldw<SMEM>(a.w, wrap_index(x0 + 32u * p, a.n));
+  for (int p = 0; p < P; ++p) wj[p] = ldw<SMEM>(a.w, checked(a, wrap_index(x0 + 32u * p, a.n)));
 }
 
 // ---------------------------------------------------------------------------
@@ -308,9 +329,11 @@ __device__ __forceinline__ void megopolis_batch(const Problem& a, const RoundKey
           }
         } else {
 #pragma unroll
-          for (int q = 0; q < U; ++q)
+          for (int q = 0; q < U; ++q) {
+            const uint32_t xq = checked(a, x0[q], 32u * (P - 1));
 #pragma unroll
-            for (int p = 0; p < P; ++p) wj[q][p] = ldw_at<SMEM>(a.w, x0[q], 32u * p);
+            for (int p = 0; p < P; ++p) wj[q][p] = ldw_at<SMEM>(a.w, xq, 32u * p);
+          }
         }
       } else {
 #pragma unroll
@@ -441,12 +464,13 @@ __device__ __forceinline__ void megopolis_short(const Problem& a, const RoundKey
       if (q < nb) {
         x0[q] = mego_column(win[b0 + q], lane);
         if (fast) {
+          const uint32_t xq = checked(a, x0[q], 32u * (P - 1));
 #pragma unroll
-          for (int p = 0; p < P; ++p) wj[q][p] = ldw_at<SMEM>(a.w, x0[q], 32u * p);
+          for (int p = 0; p < P; ++p) wj[q][p] = ldw_at<SMEM>(a.w, xq, 32u * p);
         } else {
 #pragma unroll
           for (int p = 0; p < P; ++p)
-            wj[q][p] = ldw<SMEM>(a.w, wrap_small<SMALL>(x0[q] + 32u * p, n));
+            wj[q][p] = ldw<SMEM>(a.w, checked(a, wrap_small<SMALL>(x0[q] + 32u * p, n)));
         }
       }
     }
@@ -506,7 +530,7 @@ __device__ __forceinline__ void metropolis_batch(const Problem& a, const RoundKe
       if (q < nb) {
 #pragma unroll
         for (int p = 0; p < P; ++p) {
-          jj[q][p] = index32(q == 0 ? r[p].x : r[p].z, n);
+          jj[q][p] = checked(a, index32(q == 0 ? r[p].x : r[p].z, n));
           wj[q][p] = ldw<SMEM>(a.w, jj[q][p]);
         }
       }
@@ -583,7 +607,7 @@ __device__ __forceinline__ void partition_batch(const Problem& a, const RoundKey
             const int src = ((b0 + q) % kStepsPerFill) * P + p;
             pp = __shfl_sync(0xFFFFFFFFu, part_reg, src);
           }
-          jj[q][p] = pp * a.nw + index32(q == 0 ? r[p].x : r[p].z, a.nw);
+          jj[q][p] = checked(a, pp * a.nw + index32(q == 0 ? r[p].x : r[p].z, a.nw));
           wj[q][p] = ldw<SMEM>(a.w, jj[q][p]);
         }
       }
