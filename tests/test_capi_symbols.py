@@ -80,3 +80,28 @@ def test_binding_structs_match_the_header(lib):
     for which, cls in enumerate(mirrors):
         assert lib.mego_struct_size(which) == ctypes.sizeof(cls), cls.__name__
     assert lib.mego_struct_size(99) == 0
+
+
+def test_batch_plan_size_is_host_only(lib):
+    # mego_batch_plan_bytes validates the filters and sizes the plan on the
+    # host: header, per-filter descriptors and prefix entries, the bound's
+    # per-filter outputs and one 16-byte partial per 4096-weight chunk.
+    mego = pytest.importorskip("paper_2109_13504_gb300")
+    lib.mego_batch_plan_bytes.restype = ctypes.c_size_t
+    lib.mego_batch_plan_bytes.argtypes = [ctypes.POINTER(mego.Filter), ctypes.c_int32]
+
+    def plan(sizes):
+        arr = (mego.Filter * len(sizes))()
+        for k, n in enumerate(sizes):
+            arr[k].w = 0x1000
+            arr[k].anc = 0x2000
+            arr[k].n = n
+            arr[k].B = -1
+        return lib.mego_batch_plan_bytes(arr, len(sizes))
+
+    one = plan([4096])
+    assert one > 0 and one % 256 == 0
+    assert plan([4096 * 100]) >= one + 99 * 16      # one partial per 4096-weight chunk
+    assert plan([100] * 64) > plan([100] * 8)       # descriptors grow with the count
+    assert plan([0]) == 0 and plan([(1 << 30) + 1]) == 0   # invalid sizes
+    assert lib.mego_batch_plan_bytes(None, 1) == 0
