@@ -74,6 +74,8 @@ def _hold(torch, launches):
     """Keep the GPU busy (outside any timed interval) for long enough that the
     host can enqueue `launches` library calls behind it."""
     torch.cuda._sleep(int(HOLD_US_PER_LAUNCH * launches * 2100))
+
+
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "batch_resample_sweep5_n2p20.md")
 KERNEL_SOURCES = ("resample_kernels.cuh", "device_common.cuh", "batch.cu")
 
@@ -440,11 +442,36 @@ def _sir_leg(args, mego, synthetic, torch, dev):
     return out
 
 
+def _per_launch_ms(torch, stream, flush, fn, reps):
+    """Device time of one call of fn with a cold L2: events around reps x
+    (flush, fn) minus events around reps x (flush), divided by reps, median
+    of three such runs.  Short kernels are timed back to back this way, so
+    the figure is not dominated by the event timer's granularity (about 2 us
+    here) or by the host's launch latency."""
+    import statistics as stats
+    res = []
+    for _ in range(3):
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        torch.cuda.synchronize()
+        _hold(torch, 2 * reps)
+        a.record(stream)
+        for _ in range(reps):
+            flush.zero_()
+        b.record(stream)
+        for _ in range(reps):
+            flush.zero_()
+            fn()
+        c.record(stream)
+        torch.cuda.synchronize()
+        res.append((b.elapsed_time(c) - a.elapsed_time(b)) / reps)
+    return stats.median(res)
+
+
 def _sweep_leg(args, mego, synthetic, torch, dev):
     """The scaling sweep: resample time (B computed beforehand, as the
     paper's Tables 3-4 exclude it) at N = 2^14..2^24 and y = 0..4, Megopolis
-    and Metropolis, each with its autotuned launch shape; median of a few
-    event-timed launches, L2 flushed before each."""
+    and Metropolis, each with its autotuned launch shape; per-launch device
+    time with a cold L2 (_per_launch_ms)."""
     import statistics as stats
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -460,18 +487,11 @@ def _sweep_leg(args, mego, synthetic, torch, dev):
             cell = {"B": B}
             for variant, name in ((mego.MEGOPOLIS, "megopolis"), (mego.METROPOLIS, "metropolis")):
                 cfg, _ = mego.mego_autotune(w, B, variant, anc=anc, reps=2, stream=stream)
-                ts = []
-                for _ in range(args.sweep_reps):
-                    flush.zero_()
-                    _hold(torch, 1)
-                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    a.record(stream)
-                    mego.mego_resample_gather(w, B, None, SEED, 0, variant, anc=anc, cfg=cfg,
-                                              stream=stream)
-                    b.record(stream)
-                    torch.cuda.synchronize(dev)
-                    ts.append(a.elapsed_time(b))
-                cell[name + "_ms"] = stats.median(ts)
+                cell[name + "_ms"] = _per_launch_ms(
+                    torch, stream, flush,
+                    lambda: mego.mego_resample_gather(w, B, None, SEED, 0, variant, anc=anc,
+                                                      cfg=cfg, stream=stream),
+                    max(3, args.sweep_reps))
             cell["speedup"] = cell["metropolis_ms"] / cell["megopolis_ms"]
             row[str(y)] = cell
             del w
@@ -495,18 +515,11 @@ def _path_leg(args, mego, synthetic, torch, dev):
         cell = {"B": B}
         for path, name in ((mego.PATH_GLOBAL, "global_ms"), (mego.PATH_TMA, "tma_window_ms")):
             cfg = {"ppt": 6, "threads": 128, "path": path}
-            ts = []
-            for _ in range(max(5, args.sweep_reps)):
-                flush.zero_()
-                _hold(torch, 1)
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                mego.mego_resample_gather(w, B, None, SEED, 0, mego.MEGOPOLIS, anc=anc, cfg=cfg,
-                                          stream=stream)
-                b.record(stream)
-                torch.cuda.synchronize(dev)
-                ts.append(a.elapsed_time(b))
-            cell[name] = stats.median(ts)
+            cell[name] = _per_launch_ms(
+                torch, stream, flush,
+                lambda: mego.mego_resample_gather(w, B, None, SEED, 0, mego.MEGOPOLIS, anc=anc,
+                                                  cfg=cfg, stream=stream),
+                max(5, args.sweep_reps))
         out[str(y)] = cell
     return out
 
