@@ -104,13 +104,14 @@ static void draw(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t sid,
   oracle_philox4x32_10(ctr, key, out);
 }
 
-/* u in (0,1]: one 32-bit word -> 2 - f, f = 1.m in [1,2) built from the low
- * 23 bits.  2 - f is exact (Sterbenz), so u takes the 2^23 values m*2^-23,
- * m = 1..2^23, uniformly.  (0,1] rather than [0,1): u = 0 would accept a
+/* u in (0,1]: one 32-bit word -> 2 - f, f = 1.m in [1,2) whose 23-bit
+ * fraction m is the word's top 23 bits (bits 9..31; bits 0..8 are not
+ * read).  2 - f is exact (Sterbenz), so u takes the 2^23 values k*2^-23,
+ * k = 1..2^23, uniformly.  (0,1] rather than [0,1): u = 0 would accept a
  * zero-weight proposal from a positive-weight state, and u > 1 would reject
  * an equal-weight proposal.                                               */
 float oracle_u_from_word(uint32_t word) {
-  uint32_t bits = 0x3F800000u | (word & 0x007FFFFFu);
+  uint32_t bits = 0x3F800000u | (word >> 9);
   float f;
   memcpy(&f, &bits, sizeof f);
   return 2.0f - f;
@@ -141,16 +142,17 @@ uint32_t oracle_offset(uint64_t seed, uint32_t sid, uint32_t b, uint32_t n) {
 /* The uniform u that particle i uses at Megopolis iteration b.  Five
  * consecutive iterations share one Philox call, the one for counter
  * (i, floor(b/5), sid, TAG_MEGO_U).  With q = b mod 5: q < 4 uses word q;
- * q = 4 uses the word made of the most significant bytes of words 0, 1
- * and 2 (in that order, from the least significant byte up).  The u
- * mapping reads only the low 23 bits of a word, so the five uniforms of a
+ * q = 4 uses the word whose bytes 1, 2 and 3 are the least significant
+ * bytes of words 0, 1 and 2 (byte 0 is not read).  The u mapping reads
+ * only the top 23 bits of a word (bits 9..31), so the five uniforms of a
  * call are built from disjoint bits.                                       */
 float oracle_megopolis_u(uint64_t seed, uint32_t sid, uint32_t i, uint32_t b) {
   uint32_t x[4];
   uint32_t q = b % 5u;
   draw(seed, i, b / 5u, sid, TAG_MEGO_U, x);
   if (q < 4u) return oracle_u_from_word(x[q]);
-  return oracle_u_from_word((x[0] >> 24) | ((x[1] >> 24) << 8) | ((x[2] >> 24) << 16));
+  return oracle_u_from_word(((x[0] & 0xFFu) << 8) | ((x[1] & 0xFFu) << 16) |
+                            ((x[2] & 0xFFu) << 24));
 }
 
 /* Proposal and uniform for Metropolis particle i at iteration b: two

@@ -75,17 +75,19 @@ def test_philox_matches_library_implementation():
 
 def test_u_mapping_range_and_grid():
     assert oracle.u_from_word(0) == 1.0
-    assert oracle.u_from_word(0xFF800000) == 1.0          # high bits unused
-    assert oracle.u_from_word(0x007FFFFF) == 2.0 ** -23    # smallest u > 0
-    assert oracle.u_from_word(0x00000001) == 1.0 - 2.0 ** -23
+    assert oracle.u_from_word(0x000001FF) == 1.0          # low 9 bits unused
+    assert oracle.u_from_word(0xFFFFFE00) == 2.0 ** -23    # smallest u > 0
+    assert oracle.u_from_word(0xFFFFFFFF) == 2.0 ** -23
+    assert oracle.u_from_word(0x00000200) == 1.0 - 2.0 ** -23
+    assert oracle.u_from_word(0x80000000) == 0.5
     rng = np.random.default_rng(5)
     for word in rng.integers(0, 2**32, 2000, dtype=np.uint64).tolist():
         u = oracle.u_from_word(word)
         assert 0.0 < u <= 1.0
         m = u * 2.0 ** 23
         assert m == int(m) and 1 <= m <= 2 ** 23
-        # u depends only on the low 23 bits, and maps them one-to-one
-        assert m == 2 ** 23 - (word & 0x7FFFFF)
+        # u depends only on the top 23 bits, and maps them one-to-one
+        assert m == 2 ** 23 - (word >> 9)
 
 
 def test_megopolis_u_uniform():
@@ -99,7 +101,8 @@ def test_megopolis_u_uniform():
 
 def test_megopolis_u_word_layout():
     """Iteration b of particle i reads call (i, b // 5, sid, 2): words 0..3
-    for b mod 5 < 4, the top bytes of words 0..2 for b mod 5 = 4."""
+    for b mod 5 < 4; for b mod 5 = 4, the word whose bytes 1..3 are the low
+    bytes of words 0..2."""
     seed = 0x0123456789ABCDEF
     key = [seed & 0xFFFFFFFF, seed >> 32]
     for sid in (0, 7):
@@ -107,7 +110,8 @@ def test_megopolis_u_word_layout():
             for b in range(12):
                 x = [int(v) for v in oracle.philox4x32_10([i, b // 5, sid, 2], key)]
                 q = b % 5
-                word = x[q] if q < 4 else (x[0] >> 24) | (x[1] >> 24) << 8 | (x[2] >> 24) << 16
+                word = x[q] if q < 4 else ((x[0] & 0xFF) << 8 | (x[1] & 0xFF) << 16
+                                           | (x[2] & 0xFF) << 24)
                 assert oracle.megopolis_u(seed, sid, i, b) == np.float32(oracle.u_from_word(word))
 
 
