@@ -523,3 +523,71 @@ def test_huge_weights_are_reported_not_mistaken():
     st, B_cpu, q_cpu = oracle.compute_B(w_h, 0.01)
     assert int(status.item()) == mego.MEGO_OK and _b_equal(int(B_dev.item()), B_cpu, q_cpu)
     assert abs(float(q_dev.item()) - q_cpu) <= 1e-9 * max(1.0, q_cpu)
+
+
+def _mixed_tiny_weights(n, seed):
+    """Weights with signed zeros and subnormals among ordinary ones: R6's test
+    fl(u w_k) <= w_j must then run without flush-to-zero on both sides (a
+    subnormal product or weight flushed to 0 changes the comparison)."""
+    rng = np.random.default_rng(seed)
+    w = synthetic.gaussian_weights(n, 2.0, seed).copy()
+    kind = rng.integers(0, 10, n)
+    sub = rng.integers(1, 1 << 23, n, dtype=np.uint32).view(np.float32)
+    w[kind < 3] = sub[kind < 3]                       # 30 % subnormal
+    w[kind == 3] = np.float32(-0.0)
+    w[kind == 4] = np.float32(0.0)
+    w[kind == 5] *= np.float32(2.0 ** -120)           # tiny normal: products go subnormal
+    return w
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_subnormal_and_signed_zero_weights_bit_exact(variant):
+    n = 2 * 4096 + 77
+    w_h = _mixed_tiny_weights(n, 21)
+    assert np.any(np.signbit(w_h) & (w_h == 0)) and np.any((w_h > 0) & (w_h < 2.0 ** -126))
+    st, B_cpu, q_cpu = oracle.compute_B(w_h, 0.01)
+    B_dev, status, q_dev = mego.mego_compute_B(_gpu(w_h), 0.01)
+    assert st == oracle.OK and int(status.item()) == mego.MEGO_OK
+    assert _b_equal(int(B_dev.item()), B_cpu, q_cpu)
+    assert abs(float(q_dev.item()) - q_cpu) <= 1e-9 * max(1.0, q_cpu)
+    for B in (40, B_cpu):
+        ref = oracle.resample(w_h, B, 3, variant)
+        paths = [mego.PATH_GLOBAL, mego.PATH_SMEM] + \
+            ([mego.PATH_TMA] if variant == mego.MEGOPOLIS else [])
+        for path in paths:
+            cfg = {"path": path, "ppt": 4, "threads": 128}
+            assert np.array_equal(_anc(w_h, B, 3, variant, cfg=cfg), ref), (B, path)
+    # An all-subnormal vector: valid weights, and every product u w_k is subnormal.
+    w_h = np.random.default_rng(5).integers(1, 1 << 23, n, dtype=np.uint32).view(np.float32)
+    st, B_cpu, q_cpu = oracle.compute_B(w_h, 0.01)
+    B_dev, status, _ = mego.mego_compute_B(_gpu(w_h), 0.01)
+    assert st == oracle.OK and int(status.item()) == mego.MEGO_OK
+    assert _b_equal(int(B_dev.item()), B_cpu, q_cpu)
+    assert np.array_equal(_anc(w_h, B_cpu, 4, variant), oracle.resample(w_h, B_cpu, 4, variant))
+
+
+@pytest.mark.parametrize("variant,psize", [(mego.METROPOLIS_C1, 128), (mego.METROPOLIS_C2, 512)])
+def test_subnormal_weights_partition_variants_bit_exact(variant, psize):
+    n = 8192
+    w_h = _mixed_tiny_weights(n, 22)
+    for B in (1, 33):
+        ref = oracle.resample(w_h, B, 6, variant, psize_bytes=psize)
+        assert np.array_equal(_anc(w_h, B, 6, variant, psize=psize), ref), B
+
+
+def test_subnormal_weights_in_a_batch():
+    sizes = (3000, 8192 + 5)
+    ws_h = [_mixed_tiny_weights(m, 30 + k) for k, m in enumerate(sizes)]
+    ancs = [torch.full((m,), -1, dtype=torch.int32, device=DEV) for m in sizes]
+    b = mego.Batch([{"w": _gpu(w_h), "anc": a, "B": -1, "stream_id": k}
+                    for k, (w_h, a) in enumerate(zip(ws_h, ancs))], seed=8)
+    b.bound(0.01)
+    b.resample()
+    torch.cuda.synchronize()
+    Bs = b.B.cpu().numpy().tolist()
+    for k, (w_h, a) in enumerate(zip(ws_h, ancs)):
+        st, B_cpu, q_cpu = oracle.compute_B(w_h, 0.01)
+        assert st == oracle.OK and _b_equal(Bs[k], B_cpu, q_cpu)
+        ref = oracle.resample(w_h, Bs[k], 8, mego.MEGOPOLIS, stream_id=k)
+        assert np.array_equal(a.cpu().numpy(), ref), k
+    b.close()

@@ -153,6 +153,28 @@ def test_n4_exact_distribution(variant):
     assert p > 0.01, (chi2, p)
 
 
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_n4_exact_distribution_subnormal_weights(variant):
+    # All four weights subnormal, so every product u w_k is subnormal or
+    # underflows: the exact law (numpy's IEEE binary32 with gradual
+    # underflow) holds only if the oracle neither flushes subnormals to zero
+    # (which would accept every proposal) nor rounds differently.
+    w = np.array([2.0 ** -140, 2.0 ** -128, 2.0 ** -135, 0.75 * 2.0 ** -126], dtype=np.float32)
+    assert np.all(w < np.float32(2.0 ** -126)) and np.all(w > 0)
+    B = 3
+    nseeds = 1_000_000
+    counts = oracle.ancestor_counts(w, B, 5, nseeds, variant).astype(np.float64)
+    PB = _exact_marginals(w, B)
+    flushed = _exact_marginals(np.ones(4, dtype=np.float32), B)   # what FTZ would give
+    assert np.abs(PB - flushed).max() > 0.1
+    chi2 = 0.0
+    for i in range(4):
+        expect = PB[i] * nseeds
+        chi2 += float(((counts[i] - expect) ** 2 / np.maximum(expect, 1e-12)).sum())
+    p = stats.chi2.sf(chi2, df=4 * 3)
+    assert p > 0.01, (chi2, p)
+
+
 def test_n4_detects_a_reversed_acceptance():
     # The exact law is sensitive to the direction of the acceptance test:
     # the reversed rule (accept iff u*w_j <= w_k) gives a different P^B.
