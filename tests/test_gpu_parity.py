@@ -591,3 +591,14 @@ def test_subnormal_weights_in_a_batch():
         ref = oracle.resample(w_h, Bs[k], 8, mego.MEGOPOLIS, stream_id=k)
         assert np.array_equal(a.cpu().numpy(), ref), k
     b.close()
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("n,B", [(5, mego.B_MAX), (1000, 100003), (4096 + 33, 30031)])
+def test_long_chains_up_to_the_B_cap(variant, n, B):
+    """Chains of up to MEGO_B_MAX iterations: the offset counter, the group
+    counter of the u draws and the table refills run through their whole
+    range; compared with the oracle on every particle."""
+    w_h = synthetic.gaussian_weights(n, 3.0, n)
+    ref = oracle.resample(w_h, B, 12, variant, threads=oracle.host_threads())
+    assert np.array_equal(_anc(w_h, B, 12, variant), ref)
