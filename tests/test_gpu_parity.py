@@ -602,3 +602,18 @@ def test_long_chains_up_to_the_B_cap(variant, n, B):
     w_h = synthetic.gaussian_weights(n, 3.0, n)
     ref = oracle.resample(w_h, B, 12, variant, threads=oracle.host_threads())
     assert np.array_equal(_anc(w_h, B, 12, variant), ref)
+
+
+@pytest.mark.parametrize("variant", VARIANTS + [mego.METROPOLIS_C1, mego.METROPOLIS_C2])
+def test_extreme_seeds_and_stream_ids(variant):
+    """The key is (lo32(seed), hi32(seed)) and the stream id is a counter
+    word: seeds and stream ids at the ends of their ranges give the oracle's
+    ancestors too."""
+    n = 4096
+    w_h = synthetic.gaussian_weights(n, 2.5, 77)
+    psize = 256 if variant in (mego.METROPOLIS_C1, mego.METROPOLIS_C2) else 0
+    for seed in (0, 1, 0xFFFFFFFF, 1 << 32, 0x8000000000000000, 0xFFFFFFFFFFFFFFFF):
+        for sid in (0, 0x7FFFFFFF, 0xFFFFFFFF):
+            ref = oracle.resample(w_h, 21, seed, variant, stream_id=sid, psize_bytes=psize)
+            got = _anc(w_h, 21, seed, variant, sid=sid, psize=psize)
+            assert np.array_equal(got, ref), (hex(seed), hex(sid))
