@@ -46,7 +46,7 @@ SEED = 1
 # Philox4x32-10 call serves five proposals; the 5 of its 20 wide multiplies
 # and the 3 of its 20 xors that depend only on the particle and the stream
 # are hoisted):
-#   ALU pipe (16 lanes/cycle per SM sub-partition): the u mask/or, the
+#   ALU pipe (16 lanes/cycle per SM sub-partition): the u shift/or, the
 #     compare, the two selects (state weight, accepted column) = 4, plus 17/5
 #     Philox xors and 2/5 byte permutes for the fifth uniform;
 #   FMA-heavy pipe (8 lanes/cycle for a 32x32->64-bit multiply): 15/5;
