@@ -183,15 +183,29 @@ __device__ __forceinline__ void finish_batch(const Problem& a, uint32_t ibase,
   for (int p = 0; p < P; ++p)
     if (live[p] && a.anc) (a.anc + ibase)[32u * p] = static_cast<int32_t>(k[p]);
   if constexpr (GATHER == kGatherSoa) {
-    for (int d = 0; d < a.dim; ++d) {
-      const float* src = a.x_in + static_cast<int64_t>(d) * a.ld;
-      float* dst = a.x_out + static_cast<int64_t>(d) * a.ld;
-      float v[P];
+    // Rows in rounds of three: all of a round's random loads are in flight
+    // before its stores (x_out never overlaps x_in, so the order is free),
+    // one memory latency per three rows instead of one per row.
+    constexpr int kRows = 3;
+    for (int d0 = 0; d0 < a.dim; d0 += kRows) {
+      float v[kRows][P];
 #pragma unroll
-      for (int p = 0; p < P; ++p) v[p] = live[p] ? __ldg(src + k[p]) : 0.0f;
+      for (int dd = 0; dd < kRows; ++dd) {
+        if (d0 + dd < a.dim) {
+          const float* src = a.x_in + static_cast<int64_t>(d0 + dd) * a.ld;
 #pragma unroll
-      for (int p = 0; p < P; ++p)
-        if (live[p]) (dst + ibase)[32u * p] = v[p];
+          for (int p = 0; p < P; ++p) v[dd][p] = live[p] ? __ldg(src + k[p]) : 0.0f;
+        }
+      }
+#pragma unroll
+      for (int dd = 0; dd < kRows; ++dd) {
+        if (d0 + dd < a.dim) {
+          float* dst = a.x_out + static_cast<int64_t>(d0 + dd) * a.ld;
+#pragma unroll
+          for (int p = 0; p < P; ++p)
+            if (live[p]) (dst + ibase)[32u * p] = v[dd][p];
+        }
+      }
     }
   } else if constexpr (GATHER == kGatherAos4) {
     const float4* src = reinterpret_cast<const float4*>(a.x_in);
